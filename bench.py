@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark: MLUPS of the fused collide-stream step on one GB300.
+
+Workload (one "step" = one time level of the whole hot path: pull-stream,
+moments, Hermite equilibrium, relaxation, store, FP64 diagnostics):
+standing shear wave on a periodic 4096 x 4096 grid, D2Q36 Gauss-Hermite
+product set (Lax-Wendroff streaming), third-order equilibrium, FP32 deviation
+storage, Kn = 0.1, u_y = 1e-3 sin x + 1e-3 sin y sin x.  The on-lattice D2Q37
+set on the same grid is measured alongside (per-quadrature metric).
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank runs its
+own independent instance (weak scaling, no data-path collective); the time is
+the max over ranks and the value the cell updates of all ranks per second.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (million lattice-cell updates per second), fused collide-stream step"
+WORKLOAD = "standing shear wave 4096x4096, D2Q36-GH (Lax-Wendroff), N=3, FP32 deviations, Kn=0.1"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        smax = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in ("lb_kernels.cuh", "lb_device.h", "velocity_sets.h"):
+        with open(os.path.join(ROOT, "paper_0908_4520_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(quad):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(quad)
+    if not ent or ent.get("kernel_digest") != kernel_digest():
+        return None
+    return ent.get("dram_bytes_per_full_launch")
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, diag_every_note=True):
+    stream = torch.cuda.Stream()
+    L = Lattice(quad, 3, nx, ny, kn, precision="f32", stream=stream.cuda_stream)
+    L.init_shear_wave(1e-3, 1e-3)
+    L.step(warmup)
+    L.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = L.launches
+    return L, stream, ev0, ev1, n0
+
+
+def run_gpu(args):
+    import torch
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import numpy as np
+
+    from paper_0908_4520_gb300 import Lattice, capi
+
+    nx = ny = args.n
+    ncell = nx * ny
+    results = {}
+    sampler = ClockSampler(local)
+    main_ms = None
+    launches = 0
+    for quad in (args.quad, args.also):
+        if not quad:
+            continue
+        L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if quad == args.quad:
+            sampler.start()
+            time.sleep(0.3)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            L.step(args.steps)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        if quad == args.quad:
+            sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        if quad == args.quad:
+            launches = L.launches - n0
+        rec = L.diagnostics(4)
+        ok = bool(np.all(rec["flags"] == 0))
+        info = L.info
+        bpc = info["bytes_per_cell_update"]
+        per_launch_s = ms / 1e3 / args.steps
+        results[quad] = {
+            "ms_per_step": ms / args.steps,
+            "mlups": ncell * world * args.steps / (ms / 1e3) / 1e6,
+            "algorithmic_bytes_per_cell": bpc,
+            "achieved_gbs": bpc * ncell / per_launch_s / 1e9,
+            "finite": ok,
+        }
+        if quad == args.quad:
+            main_ms = ms
+            main_L = L
+        else:
+            L.close()
+
+    # end-to-end through the C-ABI with host buffers: fields in, one record out per step, u_y back
+    L = main_L
+    e2e = None
+    if rank == 0 or world > 1:
+        x = 2 * np.pi * np.arange(nx) / nx
+        y = 2 * np.pi * np.arange(ny) / ny
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        uy_h = pin(1e-3 * np.sin(x)[None, :] + 1e-3 * np.sin(y)[:, None] * np.sin(x)[None, :])
+        rho_h = pin(np.ones((ny, nx)))
+        ux_h = pin(np.zeros((ny, nx)))
+        out_h = torch.empty((ny, nx), dtype=torch.float64).pin_memory()
+        import ctypes
+
+        dptr = lambda t: ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))
+        e2e_steps = args.e2e_steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capi.check(capi.lib.lb_init_fields(L.h, dptr(rho_h), dptr(ux_h), dptr(uy_h), None), L.h)
+        for _ in range(e2e_steps):
+            capi.lb_step(L.h, 1)
+            capi.lb_diagnostics(L.h, 1)
+        capi.check(capi.lib.lb_moments(L.h, None, None, dptr(out_h), None, None), L.h)
+        t1 = time.perf_counter()
+        el = t1 - t0
+        h2d = 3 * 8 * ncell / e2e_steps
+        d2h = (64 * e2e_steps + 8 * ncell) / e2e_steps
+        e2e = {"value": ncell * e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+               "note": "timed: lb_init_fields from pinned host rho/ux/uy, steps each followed by a diagnostics "
+                       "record read, final u_y read-back; bytes amortised per step"}
+    L.close()
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    main = results[args.quad]
+    peak, peak_kind = peaks()
+    bpc = main["algorithmic_bytes_per_cell"]
+    achieved = main["achieved_gbs"]
+    traffic = ncu_traffic(args.quad)
+    cpu = cpu_baseline(args) if not args.no_cpu else None
+    line = {
+        "metric": METRIC,
+        "value": round(main["mlups"], 2),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(main_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (analytic shear-wave initial condition, seeded; no dataset)",
+        "config": {"workload": WORKLOAD, "quadrature": args.quad, "n_eq": 3, "nx": nx, "ny": ny, "kn": args.kn,
+                   "u0": 1e-3, "u1": 1e-3, "storage": "f32 deviation f - w rho0",
+                   "diagnostics": "every step (fused)",
+                   "l2": "inputs larger than L2: two population buffers of %.2f GB each" % (bpc / 2 * ncell / 1e9),
+                   "parallelism": f"independent instance per GPU x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "lb_fused_kernel<GH6,3,float,float,2,kStep>",
+                     "algorithmic_bytes_per_launch": bpc * ncell},
+        "per_quadrature": {q: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+                           | {"roofline_frac": round(r["achieved_gbs"] / peak, 4)} for q, r in results.items()},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": sampler.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) legs
+
+def oracle_sample(quad, rows, steps, kn):
+    import oracle
+
+    oracle.build()
+    P = oracle.Problem(quad, 3, 4096, rows, kn)
+    f = P.init_shear(1e-3, 1e-3)
+    t0 = time.perf_counter()
+    P.run(f, steps, record=True)
+    el = time.perf_counter() - t0
+    return 4096 * rows * steps / el / 1e6, el
+
+
+def cpu_baseline(args):
+    mlups, el = oracle_sample(args.quad, args.cpu_rows, args.cpu_steps, args.kn)
+    return {"value": round(mlups, 5), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {args.quad} N=3, periodic 4096x{args.cpu_rows} slab of the workload, "
+                      f"{args.cpu_steps} steps with records ({el:.1f} s), single thread"}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        oracle_sample(args.quad, args.ref_rows, 1, args.kn)
+    total_cells = 0
+    total_t = 0.0
+    for _ in range(args.steps):
+        m, el = oracle_sample(args.quad, args.ref_rows, 1, args.kn)
+        total_cells += 4096 * args.ref_rows
+        total_t += el
+        steps.append(el)
+    value = total_cells / total_t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total_t / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (analytic shear-wave initial condition)",
+        "config": {"workload": WORKLOAD, "quadrature": args.quad, "n_eq": 3, "nx": 4096, "ny": args.ref_rows,
+                   "kn": args.kn, "note": "each step: one time level of the oracle on a periodic 4096 x "
+                                          f"{args.ref_rows} slab (bounded sample of the 4096^2 workload)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"4096x{args.ref_rows} slab, one time level per step"},
+        "e2e": {"value": round(value, 5), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quad", default="D2Q36-GH")
+    ap.add_argument("--also", default="D2Q37", help="second quadrature measured on the same grid ('' = none)")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--kn", type=float, default=0.1)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-rows", type=int, default=48)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

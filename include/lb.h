@@ -1,0 +1,182 @@
+/*
+ * lb.h - C-ABI of the GB300 high-order lattice Boltzmann library (liblb.so).
+ *
+ * One handle = one periodic nx x ny lattice advanced by the fused BGK
+ * collide-stream update of the paper (Meng & Zhang, "Accuracy analysis of
+ * high-order lattice Boltzmann models for rarefied gas flows"):
+ *   moments    rho = sum f~, rho u = sum xi f~, 2 rho T = sum |xi - u|^2 f~  (Sec. 2.2)
+ *   equilibrium Hermite expansion of the Maxwellian truncated at order N     (Sec. 2.1,
+ *              Eqs. approxf, an, demoeq)
+ *   collision  f* = f~ - omega (f~ - f^eq), omega = dt / (tau + dt/2)         (Eq. 2order)
+ *   streaming  exact shift along integer e_alpha for on-lattice sets (Table 1),
+ *              Lax-Wendroff for off-lattice Gauss-Hermite product sets
+ *              (Sec. 2.3; Sec. 3.3; caption of the D2Q400 figure)
+ *
+ * Conventions (every function):
+ *  - Returns lb_status; nothing is thrown across the ABI.  Out-pointers are
+ *    written only on LB_OK.  lb_last_error(h) holds a human-readable message
+ *    for the handle's last failure.
+ *  - The library owns all device memory of a handle (optionally through the
+ *    caller's allocator callbacks in lb_params).  The caller owns host arrays.
+ *  - Work is enqueued on the handle's CUDA stream.  lb_step returns after
+ *    enqueueing; device-side errors (non-finite state) surface at the next
+ *    synchronising call (lb_moments, lb_diagnostics, lb_synchronize).
+ *  - A handle is not thread-safe; different handles may be used from
+ *    different threads and run concurrently on different streams.
+ *
+ * Units (Eq. nondime): lengths in 1/theta, velocities in sqrt(R T0), so the
+ * grid spacing is dx = dy = 2 pi / nx and rho0 = T0 = 1.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,          /* invalid argument (sizes, NULL handle, omega out of (0,2), ...) */
+    LB_ERR_UNSUPPORTED = -2,  /* valid request this build does not provide */
+    LB_ERR_NOMEM = -3,        /* device or host allocation failed */
+    LB_ERR_CUDA = -4,         /* CUDA runtime error (message in lb_last_error) */
+    LB_ERR_UNSTABLE = -5,     /* the state became non-finite */
+    LB_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
+    LB_ERR_BUDGET = -7,       /* request exceeds the configured device-memory budget */
+    LB_ERR_STATE = -8         /* call out of order (e.g. lb_step before an init) */
+} lb_status;
+
+/* Velocity sets.  *_GH: tensor products of the n-point Gauss-Hermite rule
+ * (off-lattice, Lax-Wendroff streaming).  The others are on-lattice
+ * (xi = c e, e integer, exact shift): D2Q9, D2Q16 (m=1,n=4), D2Q17, D2Q21
+ * and D2Q25 (m=3,n=7) from Table 1; D2Q37 (degree 9, |e| <= 3) is built by
+ * moment matching over integer shells (the search of Sec. 2.3). */
+typedef enum {
+    LB_D2Q16_GH = 0,
+    LB_D2Q36_GH = 1,
+    LB_D2Q64_GH = 2,
+    LB_D2Q37 = 3,
+    LB_D2Q9 = 4,
+    LB_D2Q16_INT = 5,
+    LB_D2Q17 = 6,
+    LB_D2Q21 = 7,
+    LB_D2Q25 = 8
+} lb_quadrature;
+
+/* Storage of the populations.  F32/F64 store the deviation f~ - w rho0;
+ * BF16/F16 store (f~ - w rho0) / (w S) with a per-handle scale S.  The
+ * arithmetic is FP32 for F32/BF16/F16 and FP64 for F64. */
+typedef enum { LB_F32 = 0, LB_F64 = 1, LB_BF16 = 2, LB_F16 = 3 } lb_precision;
+
+/* How kn maps to the collision time tau of Eq. bgk.
+ * LAMBDA: kn is lambda/L with lambda = mu/p sqrt(pi R T/2), tau = kn sqrt(2/pi).
+ * PAPER:  kn is Eq. KN, tau = kn. */
+typedef enum { LB_KN_LAMBDA = 0, LB_KN_PAPER = 1 } lb_kn_convention;
+
+typedef struct {
+    lb_quadrature quadrature;
+    int n_eq;                  /* Hermite order N of the equilibrium, 2..4 */
+    int nx, ny;                /* periodic grid; nx even, >= 2; ny >= 1 */
+    double kn;                 /* Knudsen number (> 0), see kn_convention */
+    lb_precision precision;    /* default LB_F32 */
+    lb_kn_convention kn_convention; /* default LB_KN_LAMBDA */
+    double cfl;                /* off-lattice only: dt = cfl dx / max|xi_x|, 0 < cfl <= 1 (default 1) */
+    int isothermal;            /* 1: T = 1 in the equilibrium (default 0: kinetic T) */
+    int diag_capacity;         /* records kept in the device ring (default 65536) */
+    double storage_scale;      /* 16-bit scale S; 0 = set at init from the amplitude */
+    void *stream;              /* cudaStream_t to run on; NULL = a stream the handle creates */
+    /* optional device allocator (e.g. PyTorch's caching allocator); both or neither */
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+    void *alloc_ctx;
+} lb_params;
+
+/* One diagnostics record per time level n (t = n dt), FP64 sums over the grid:
+ * mass = sum rho, mom_x/mom_y = sum rho u, amp = 2/(nx ny) sum u_y sin(x_i),
+ * shear = 2/(nx ny) sum sigma_xy cos(x_i) with sigma_xy = (1 - omega/2)
+ * sum xi_x xi_y (f~ - f^eq) (pressure-tensor sign), hnorm = sum (f~ - w rho0)^2 / w,
+ * x_i = i dx.  flags != 0 marks a non-finite sum. */
+typedef struct {
+    double t, mass, mom_x, mom_y, amp, shear, hnorm, flags;
+} lb_diag;
+
+typedef struct {
+    int q;              /* number of velocities */
+    int degree;         /* exact polynomial degree of the quadrature */
+    int on_lattice;     /* 1: exact shift streaming, 0: Lax-Wendroff */
+    int halo;           /* max |e| (on-lattice) or 1 (Lax-Wendroff) */
+    double dx, dt, tau, omega;
+    double c_lattice;   /* xi = c e for on-lattice sets, else 0 */
+    long long time_level;   /* n: the state is f~(n dt) */
+    long long records;      /* diagnostics records produced so far (n + 1 after init) */
+    size_t bytes_per_cell_update; /* algorithmic HBM bytes: 2 q sizeof(storage) */
+    size_t device_bytes;    /* device memory held by the handle */
+    double storage_scale;   /* 16-bit scale S (1 for F32/F64) */
+} lb_info_t;
+
+/* Fill *p with defaults (F32, LAMBDA, cfl 1, kinetic T, own stream). */
+void lb_params_default(lb_params *p);
+
+/* Create a handle with default parameters.  Host work + device allocation; no launch. */
+lb_status lb_create(lb_quadrature q, int n_eq, int nx, int ny, double kn, lb_handle **out);
+lb_status lb_create_ex(const lb_params *p, lb_handle **out);
+
+/* Standing shear wave at rest density and temperature (Sec. 4):
+ * rho = 1, T = 1, u_x = 0, u_y = u0 sin(x_i) + u1 sin(2 pi j / ny) sin(x_i),
+ * f~(0) = f^eq.  Resets time to 0 and records level 0. */
+lb_status lb_init_shear_wave(lb_handle *h, double u0, double u1);
+
+/* f~(0) = f^eq(rho, u, T) from caller host arrays of nx*ny doubles, row-major
+ * (index j*nx + i); T may be NULL (T = 1).  Resets time to 0. */
+lb_status lb_init_fields(lb_handle *h, const double *rho, const double *ux, const double *uy,
+                         const double *T);
+
+/* Advance n >= 0 time levels (asynchronous; CUDA-graph replay). */
+lb_status lb_step(lb_handle *h, int n);
+
+/* Moments of f~ at the current time level into caller host arrays of nx*ny
+ * doubles (any may be NULL).  Synchronises the handle's stream. */
+lb_status lb_moments(lb_handle *h, double *rho, double *ux, double *uy, double *T, double *sxy);
+
+/* Same, into caller DEVICE arrays of nx*ny doubles, asynchronous on the stream. */
+lb_status lb_moments_device(lb_handle *h, double *rho, double *ux, double *uy, double *T,
+                            double *sxy);
+
+/* f~ at the current level as FP64 (full f, not the deviation), q*ny*nx doubles,
+ * index (alpha*ny + j)*nx + i, into a caller host array.  Synchronises. */
+lb_status lb_populations(lb_handle *h, double *f);
+
+/* Copy the most recent min(records, capacity, max_records) diagnostics records,
+ * oldest first, into out; *n_out receives the count.  Synchronises. */
+lb_status lb_diagnostics(lb_handle *h, lb_diag *out, int max_records, int *n_out);
+
+/* Wait for the handle's work; reports device-side errors. */
+lb_status lb_synchronize(lb_handle *h);
+
+lb_status lb_get_info(const lb_handle *h, lb_info_t *out);
+
+/* Number of kernels the handle has launched (graph replays count each node). */
+long long lb_kernel_launches(const lb_handle *h);
+
+/* NULL-safe. */
+lb_status lb_destroy(lb_handle *h);
+
+const char *lb_status_string(lb_status s);
+const char *lb_last_error(const lb_handle *h);
+
+/* Host-only: the velocity set the library builds (no device needed).
+ * xi: 2q doubles (xi_x, xi_y per velocity), w: q doubles, e: 2q ints or NULL
+ * (on-lattice only); pass NULL arrays to query *q and *degree only. */
+lb_status lb_quadrature_info(lb_quadrature quad, int *q, int *degree, double *xi, double *w,
+                             int *e);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

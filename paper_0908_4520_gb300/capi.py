@@ -1,0 +1,213 @@
+"""ctypes binding of liblb.so (include/lb.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of the method; all compute runs in the library's CUDA kernels.
+Importing this module loads liblb.so and raises if it is missing: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblb.so")
+
+# lb_status
+LB_OK, LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_NOMEM, LB_ERR_CUDA = 0, -1, -2, -3, -4
+LB_ERR_UNSTABLE, LB_ERR_TIMEOUT, LB_ERR_BUDGET, LB_ERR_STATE = -5, -6, -7, -8
+
+# lb_quadrature
+QUADRATURES = {
+    "D2Q16-GH": 0, "D2Q36-GH": 1, "D2Q64-GH": 2, "D2Q37": 3, "D2Q9": 4,
+    "D2Q16-int": 5, "D2Q17": 6, "D2Q21": 7, "D2Q25": 8,
+}
+# lb_precision
+PRECISIONS = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
+KN_LAMBDA, KN_PAPER = 0, 1
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [
+        ("quadrature", ctypes.c_int), ("n_eq", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("kn", ctypes.c_double), ("precision", ctypes.c_int), ("kn_convention", ctypes.c_int),
+        ("cfl", ctypes.c_double), ("isothermal", ctypes.c_int), ("diag_capacity", ctypes.c_int),
+        ("storage_scale", ctypes.c_double), ("stream", ctypes.c_void_p),
+        ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class lb_diag(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("t", "mass", "mom_x", "mom_y", "amp", "shear", "hnorm", "flags")]
+
+
+DIAG_DTYPE = np.dtype([(k, np.float64) for k in ("t", "mass", "mom_x", "mom_y", "amp", "shear", "hnorm", "flags")])
+
+
+class lb_info_t(ctypes.Structure):
+    _fields_ = [
+        ("q", ctypes.c_int), ("degree", ctypes.c_int), ("on_lattice", ctypes.c_int), ("halo", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double),
+        ("c_lattice", ctypes.c_double), ("time_level", ctypes.c_longlong), ("records", ctypes.c_longlong),
+        ("bytes_per_cell_update", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
+        ("storage_scale", ctypes.c_double),
+    ]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "lb_params_default": (None, [ctypes.POINTER(lb_params)]),
+        "lb_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(H)]),
+        "lb_create_ex": (ctypes.c_int, [ctypes.POINTER(lb_params), ctypes.POINTER(H)]),
+        "lb_init_shear_wave": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_double]),
+        "lb_init_fields": (ctypes.c_int, [H, dp, dp, dp, dp]),
+        "lb_step": (ctypes.c_int, [H, ctypes.c_int]),
+        "lb_moments": (ctypes.c_int, [H, dp, dp, dp, dp, dp]),
+        "lb_moments_device": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+        "lb_populations": (ctypes.c_int, [H, dp]),
+        "lb_diagnostics": (ctypes.c_int, [H, ctypes.POINTER(lb_diag), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "lb_synchronize": (ctypes.c_int, [H]),
+        "lb_get_info": (ctypes.c_int, [H, ctypes.POINTER(lb_info_t)]),
+        "lb_kernel_launches": (ctypes.c_longlong, [H]),
+        "lb_destroy": (ctypes.c_int, [H]),
+        "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "lb_last_error": (ctypes.c_char_p, [H]),
+        "lb_quadrature_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), dp, dp,
+                                              ctypes.POINTER(ctypes.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+# declared entry points of include/lb.h (checked against the library's exports by the tests)
+EXPORTS = [
+    "lb_params_default", "lb_create", "lb_create_ex", "lb_init_shear_wave", "lb_init_fields", "lb_step",
+    "lb_moments", "lb_moments_device", "lb_populations", "lb_diagnostics", "lb_synchronize", "lb_get_info",
+    "lb_kernel_launches", "lb_destroy", "lb_status_string", "lb_last_error", "lb_quadrature_info",
+]
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{lib.lb_status_string(status).decode()} ({status}): {message}")
+        self.status = status
+
+
+def check(status: int, handle=None):
+    if status != LB_OK:
+        msg = lib.lb_last_error(handle)
+        raise LBError(status, msg.decode() if msg else "")
+    return status
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- thin wrappers with the C names --------------------------------------------------
+
+def lb_params_default() -> lb_params:
+    p = lb_params()
+    lib.lb_params_default(ctypes.byref(p))
+    return p
+
+
+def lb_create(quadrature, n_eq: int, nx: int, ny: int, kn: float):
+    h = ctypes.c_void_p()
+    q = QUADRATURES[quadrature] if isinstance(quadrature, str) else int(quadrature)
+    st = lib.lb_create(q, n_eq, nx, ny, kn, ctypes.byref(h))
+    check(st)
+    return h
+
+
+def lb_create_ex(p: lb_params):
+    h = ctypes.c_void_p()
+    check(lib.lb_create_ex(ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def lb_init_shear_wave(h, u0: float, u1: float = 0.0):
+    return check(lib.lb_init_shear_wave(h, u0, u1), h)
+
+
+def lb_init_fields(h, rho, ux, uy, T=None):
+    return check(lib.lb_init_fields(h, _dptr(rho), _dptr(ux), _dptr(uy), _dptr(T)), h)
+
+
+def lb_step(h, n: int):
+    return check(lib.lb_step(h, int(n)), h)
+
+
+def lb_moments(h, rho=None, ux=None, uy=None, T=None, sxy=None):
+    return check(lib.lb_moments(h, _dptr(rho), _dptr(ux), _dptr(uy), _dptr(T), _dptr(sxy)), h)
+
+
+def lb_moments_device(h, rho=0, ux=0, uy=0, T=0, sxy=0):
+    """Device pointers as integers (0 = skip), e.g. tensor.data_ptr()."""
+    return check(lib.lb_moments_device(h, rho or None, ux or None, uy or None, T or None, sxy or None), h)
+
+
+def lb_populations(h, f):
+    return check(lib.lb_populations(h, _dptr(f)), h)
+
+
+def lb_diagnostics(h, max_records: int):
+    out = (lb_diag * max(1, max_records))()
+    n = ctypes.c_int(0)
+    check(lib.lb_diagnostics(h, out, max_records, ctypes.byref(n)), h)
+    arr = np.frombuffer(out, dtype=DIAG_DTYPE, count=n.value).copy()
+    return arr
+
+
+def lb_synchronize(h):
+    return check(lib.lb_synchronize(h), h)
+
+
+def lb_get_info(h) -> lb_info_t:
+    info = lb_info_t()
+    check(lib.lb_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def lb_kernel_launches(h) -> int:
+    return int(lib.lb_kernel_launches(h))
+
+
+def lb_destroy(h):
+    return check(lib.lb_destroy(h))
+
+
+def lb_quadrature_info(quadrature):
+    q = QUADRATURES[quadrature] if isinstance(quadrature, str) else int(quadrature)
+    nq, deg = ctypes.c_int(), ctypes.c_int()
+    check(lib.lb_quadrature_info(q, ctypes.byref(nq), ctypes.byref(deg), None, None, None))
+    xi = np.empty(2 * nq.value)
+    w = np.empty(nq.value)
+    check(lib.lb_quadrature_info(q, None, None, _dptr(xi), _dptr(w), None))
+    e = None
+    if q >= 3:
+        e_arr = (ctypes.c_int * (2 * nq.value))()
+        check(lib.lb_quadrature_info(q, None, None, None, None, e_arr))
+        e = np.array(e_arr, dtype=np.int64).reshape(-1, 2)
+    return {"q": nq.value, "degree": deg.value, "xi": xi.reshape(-1, 2), "w": w, "e": e}

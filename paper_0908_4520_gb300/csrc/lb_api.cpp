@@ -1,0 +1,699 @@
+// C-ABI of liblb.so: handles, device memory, step constants, CUDA-graph
+// stepping, moments and diagnostics read-back.  Every compute step runs in
+// the kernels of lb_kernels.cuh; this file only marshals.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lb.h"
+#include "lb_device.h"
+#include "lb_host.h"
+
+namespace lbk {
+#define LB_DECL(set) \
+    cudaError_t launch_##set##_f32(const Launch&); \
+    cudaError_t launch_##set##_f64(const Launch&);
+#define LB_DECL16(set) \
+    LB_DECL(set)       \
+    cudaError_t launch_##set##_bf16(const Launch&); \
+    cudaError_t launch_##set##_f16(const Launch&);
+LB_DECL16(gh4)
+LB_DECL16(gh6)
+LB_DECL16(gh8)
+LB_DECL(d2q37)
+LB_DECL(d2q9)
+LB_DECL(d2q16i)
+LB_DECL(d2q17)
+LB_DECL(d2q21)
+LB_DECL(d2q25)
+#undef LB_DECL
+#undef LB_DECL16
+}  // namespace lbk
+
+namespace {
+
+using LaunchFn = cudaError_t (*)(const lbk::Launch&);
+
+LaunchFn pick_launcher(lb_quadrature q, lb_precision p) {
+#define LB_CASE(Q, set)                                      \
+    case Q:                                                  \
+        switch (p) {                                         \
+            case LB_F32: return lbk::launch_##set##_f32;     \
+            case LB_F64: return lbk::launch_##set##_f64;     \
+            default: return nullptr;                         \
+        }
+#define LB_CASE16(Q, set)                                    \
+    case Q:                                                  \
+        switch (p) {                                         \
+            case LB_F32: return lbk::launch_##set##_f32;     \
+            case LB_F64: return lbk::launch_##set##_f64;     \
+            case LB_BF16: return lbk::launch_##set##_bf16;   \
+            case LB_F16: return lbk::launch_##set##_f16;     \
+            default: return nullptr;                         \
+        }
+    switch (q) {
+        LB_CASE16(LB_D2Q16_GH, gh4)
+        LB_CASE16(LB_D2Q36_GH, gh6)
+        LB_CASE16(LB_D2Q64_GH, gh8)
+        LB_CASE(LB_D2Q37, d2q37)
+        LB_CASE(LB_D2Q9, d2q9)
+        LB_CASE(LB_D2Q16_INT, d2q16i)
+        LB_CASE(LB_D2Q17, d2q17)
+        LB_CASE(LB_D2Q21, d2q21)
+        LB_CASE(LB_D2Q25, d2q25)
+        default: return nullptr;
+    }
+#undef LB_CASE
+#undef LB_CASE16
+}
+
+thread_local std::string g_create_error;
+
+size_t storage_bytes(lb_precision p) {
+    switch (p) {
+        case LB_F64: return 8;
+        case LB_BF16:
+        case LB_F16: return 2;
+        default: return 4;
+    }
+}
+
+double hermite_he(int k, double x) {
+    double h0 = 1.0, h1 = x;
+    if (k == 0) return 1.0;
+    for (int j = 1; j < k; ++j) {
+        const double h2 = x * h1 - j * h0;
+        h0 = h1;
+        h1 = h2;
+    }
+    return h1;
+}
+
+int sm_count() {
+    static int n = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+    });
+    return n;
+}
+
+}  // namespace
+
+struct lb_handle {
+    lb_params p{};
+    lbh::VelocitySetInfo vs;
+    LaunchFn launch = nullptr;
+    int V = 2, pitch = 0, ntiles_x = 0, ntiles = 0, grid = 0, grid_init = 0;
+    long long plane = 0, ncell = 0;
+    size_t pop_bytes = 0, device_bytes = 0;
+    double dx = 0, dt = 0, tau = 0, omega = 0, scale = 1.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool raw_prev = true, initialized = false;
+    long long level = 0, launches = 0;
+    void* sin_d = nullptr;
+    void* cos_d = nullptr;
+    double* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    long long* level_d = nullptr;
+    lb_diag* ring = nullptr;
+    int* status = nullptr;
+    double* mom = nullptr;   // 5 * ncell scratch for lb_moments
+    double* pop = nullptr;   // q * ncell scratch for lb_populations
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    cudaGraphExec_t pair[2] = {nullptr, nullptr};
+    std::vector<std::pair<void*, size_t>> allocs;
+    std::string err;
+
+    lb_status fail(lb_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    lb_status cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return LB_ERR_CUDA;
+    }
+    void* dalloc(size_t bytes) {
+        void* ptr = nullptr;
+        if (p.alloc) {
+            ptr = p.alloc(p.alloc_ctx, bytes, stream);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+        }
+        if (ptr) {
+            allocs.push_back({ptr, bytes});
+            device_bytes += bytes;
+        }
+        return ptr;
+    }
+    void release() {
+        for (int i = 0; i < 2; ++i) {
+            if (chunk[i]) cudaGraphExecDestroy(chunk[i]);
+            if (pair[i]) cudaGraphExecDestroy(pair[i]);
+            chunk[i] = pair[i] = nullptr;
+        }
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto& a : allocs) {
+            if (p.free) p.free(p.alloc_ctx, a.first, a.second, stream);
+            else cudaFree(a.first);
+        }
+        allocs.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+
+    template <class R>
+    void fill_args(lbk::Args<R>& A) const {
+        std::memset(&A, 0, sizeof(A));
+        A.plane = plane;
+        A.nx = p.nx;
+        A.ny = p.ny;
+        A.pitch = pitch;
+        A.ntiles_x = ntiles_x;
+        A.ntiles = ntiles;
+        A.isothermal = p.isothermal;
+        A.diag_every = 1;
+        A.omega = (R)omega;
+        A.rho0 = (R)1.0;
+        A.sigma_fac = (R)(1.0 - 0.5 * omega);
+        A.dt = dt;
+        A.sinx = static_cast<const R*>(sin_d);
+        A.cosx = static_cast<const R*>(cos_d);
+        A.partials = partials;
+        A.ticket = ticket;
+        A.level = level_d;
+        A.ring = ring;
+        A.ring_cap = p.diag_capacity;
+        A.status = status;
+        lbk::Tab<R>& t = A.tab;
+        for (int i = 0; i < vs.na; ++i) {
+            t.a[i] = (R)vs.axis[i];
+            double fact = 1.0;
+            for (int k = 0; k <= lbk::kMaxN; ++k) {
+                if (k > 1) fact *= k;
+                t.hn[i][k] = (R)(hermite_he(k, vs.axis[i]) / fact);
+            }
+            const double C = vs.on_lattice ? 0.0 : vs.axis[i] * dt / dx;
+            t.lw[i][0] = (R)(0.5 * C * (1.0 + C));
+            t.lw[i][1] = (R)(1.0 - C * C);
+            t.lw[i][2] = (R)(-0.5 * C * (1.0 - C));
+        }
+        for (int a = 0; a < vs.q; ++a) {
+            t.w[a] = (R)vs.w[a];
+            t.winv[a] = (R)(1.0 / vs.w[a]);
+            t.xixy[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a + 1]);
+            t.xi2[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a] + vs.xi[2 * a + 1] * vs.xi[2 * a + 1]);
+            t.sc[a] = (R)(vs.w[a] * scale);
+            t.scinv[a] = (R)(1.0 / (vs.w[a] * scale));
+        }
+    }
+
+};
+
+namespace {
+
+template <class R>
+lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int raw, int grid,
+                      double* o_rho, double* o_ux, double* o_uy, double* o_T, double* o_sxy, double* o_pop,
+                      double u0, double u1, const double* i_rho, const double* i_ux, const double* i_uy,
+                      const double* i_T) {
+    lbk::Args<R> A;
+    h->fill_args(A);
+    A.src = src;
+    A.dst = dst;
+    A.raw = raw;
+    A.o_rho = o_rho;
+    A.o_ux = o_ux;
+    A.o_uy = o_uy;
+    A.o_T = o_T;
+    A.o_sxy = o_sxy;
+    A.o_pop = o_pop;
+    A.u0 = u0;
+    A.u1 = u1;
+    A.i_rho = i_rho;
+    A.i_ux = i_ux;
+    A.i_uy = i_uy;
+    A.i_T = i_T;
+    lbk::Launch L;
+    L.kind = kind;
+    L.n_eq = h->p.n_eq;
+    L.prec = h->p.precision;
+    L.grid = grid;
+    L.stream = h->stream;
+    L.args = &A;
+    const cudaError_t e = h->launch(L);
+    if (e != cudaSuccess) return h->cuda_fail(e, "kernel launch");
+    ++h->launches;
+    return LB_OK;
+}
+
+lb_status launch_any(lb_handle* h, int kind, const void* src, void* dst, int raw, int grid,
+                     double* o_rho = nullptr, double* o_ux = nullptr, double* o_uy = nullptr,
+                     double* o_T = nullptr, double* o_sxy = nullptr, double* o_pop = nullptr,
+                     double u0 = 0, double u1 = 0, const double* i_rho = nullptr,
+                     const double* i_ux = nullptr, const double* i_uy = nullptr,
+                     const double* i_T = nullptr) {
+    if (h->p.precision == LB_F64)
+        return launch_with<double>(h, kind, src, dst, raw, grid, o_rho, o_ux, o_uy, o_T, o_sxy, o_pop, u0, u1,
+                                   i_rho, i_ux, i_uy, i_T);
+    return launch_with<float>(h, kind, src, dst, raw, grid, o_rho, o_ux, o_uy, o_T, o_sxy, o_pop, u0, u1, i_rho,
+                              i_ux, i_uy, i_T);
+}
+
+// One step launch: level n -> n+1 (src = buf[cur] holds f*(n-1), dst gets f*(n)).
+lb_status step_once(lb_handle* h, int from) {
+    return launch_any(h, lbk::kStep, h->buf[from], h->buf[1 - from], 0, h->grid);
+}
+
+lb_status build_graph(lb_handle* h, int from, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamBeginCapture");
+    const long long before = h->launches;
+    lb_status st = LB_OK;
+    int b = from;
+    for (int i = 0; i < nsteps && st == LB_OK; ++i) {
+        st = step_once(h, b);
+        b = 1 - b;
+    }
+    e = cudaStreamEndCapture(h->stream, &g);
+    h->launches = before;  // captured launches are counted at replay
+    if (st != LB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaGraphInstantiate");
+    return LB_OK;
+}
+
+constexpr int kChunk = 32;
+
+lb_status set_scale_and_tables(lb_handle* h, double amp) {
+    if (h->p.precision == LB_BF16 || h->p.precision == LB_F16) {
+        double s = h->p.storage_scale;
+        if (s <= 0) s = std::max(2.0 * amp, 1e-6);
+        h->scale = s;
+    } else {
+        h->scale = 1.0;
+    }
+    // graphs bake the tables into their kernel parameters: rebuild on change
+    for (int i = 0; i < 2; ++i) {
+        if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
+        if (h->pair[i]) cudaGraphExecDestroy(h->pair[i]);
+        h->chunk[i] = h->pair[i] = nullptr;
+    }
+    return LB_OK;
+}
+
+lb_status init_common(lb_handle* h, double u0, double u1, const double* d_rho, const double* d_ux,
+                      const double* d_uy, const double* d_T) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->level_d, 0, sizeof(long long), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaMemsetAsync");
+    lb_status st = launch_any(h, lbk::kInit, nullptr, h->buf[1], 0, h->grid_init, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, nullptr, u0, u1, d_rho, d_ux, d_uy, d_T);
+    if (st != LB_OK) return st;
+    // level 0: collide f~(0) (no streaming) -> f*(0) in buf[0], record 0
+    st = launch_any(h, lbk::kStep, h->buf[1], h->buf[0], 1, h->grid);
+    if (st != LB_OK) return st;
+    h->cur = 0;
+    h->raw_prev = true;
+    h->level = 0;
+    h->initialized = true;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_params_default(lb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->quadrature = LB_D2Q16_GH;
+    p->n_eq = 2;
+    p->nx = 64;
+    p->ny = 1;
+    p->kn = 0.1;
+    p->precision = LB_F32;
+    p->kn_convention = LB_KN_LAMBDA;
+    p->cfl = 1.0;
+    p->isothermal = 0;
+    p->diag_capacity = 65536;
+    p->storage_scale = 0.0;
+}
+
+const char* lb_status_string(lb_status s) {
+    switch (s) {
+        case LB_OK: return "ok";
+        case LB_ERR_ARG: return "invalid argument";
+        case LB_ERR_UNSUPPORTED: return "unsupported";
+        case LB_ERR_NOMEM: return "out of memory";
+        case LB_ERR_CUDA: return "CUDA error";
+        case LB_ERR_UNSTABLE: return "non-finite state";
+        case LB_ERR_TIMEOUT: return "device wait timed out";
+        case LB_ERR_BUDGET: return "over device-memory budget";
+        case LB_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* lb_last_error(const lb_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+lb_status lb_quadrature_info(lb_quadrature quad, int* q, int* degree, double* xi, double* w, int* e) {
+    lbh::VelocitySetInfo vs;
+    std::string err;
+    if (!lbh::build_velocity_set(quad, &vs, &err)) {
+        g_create_error = err;
+        return LB_ERR_ARG;
+    }
+    if (q) *q = vs.q;
+    if (degree) *degree = vs.degree;
+    if (xi) std::copy(vs.xi.begin(), vs.xi.end(), xi);
+    if (w) std::copy(vs.w.begin(), vs.w.end(), w);
+    if (e) {
+        if (!vs.on_lattice) return LB_ERR_ARG;
+        for (int a = 0; a < vs.q; ++a) {
+            e[2 * a] = vs.ex[a];
+            e[2 * a + 1] = vs.ey[a];
+        }
+    }
+    return LB_OK;
+}
+
+lb_status lb_create(lb_quadrature q, int n_eq, int nx, int ny, double kn, lb_handle** out) {
+    lb_params p;
+    lb_params_default(&p);
+    p.quadrature = q;
+    p.n_eq = n_eq;
+    p.nx = nx;
+    p.ny = ny;
+    p.kn = kn;
+    return lb_create_ex(&p, out);
+}
+
+lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
+    if (!pin || !out) {
+        g_create_error = "null argument";
+        return LB_ERR_ARG;
+    }
+    const lb_params& P = *pin;
+    auto reject = [](lb_status s, const std::string& m) {
+        g_create_error = m;
+        return s;
+    };
+    if (P.nx < 2 || (P.nx & 1)) return reject(LB_ERR_ARG, "nx must be even and >= 2");
+    if (P.ny < 1) return reject(LB_ERR_ARG, "ny must be >= 1");
+    if ((long long)P.nx * P.ny > (1LL << 31) - 1) return reject(LB_ERR_ARG, "grid too large");
+    if (P.n_eq < 2 || P.n_eq > 4) return reject(LB_ERR_ARG, "n_eq must be 2, 3 or 4");
+    if (!(P.kn > 0) || !std::isfinite(P.kn)) return reject(LB_ERR_ARG, "kn must be positive");
+    if (!(P.cfl > 0 && P.cfl <= 1.0)) return reject(LB_ERR_ARG, "cfl must be in (0, 1]");
+    if (P.diag_capacity < 1) return reject(LB_ERR_ARG, "diag_capacity must be >= 1");
+    if ((P.alloc == nullptr) != (P.free == nullptr)) return reject(LB_ERR_ARG, "alloc and free go together");
+    if (P.kn_convention != LB_KN_LAMBDA && P.kn_convention != LB_KN_PAPER)
+        return reject(LB_ERR_ARG, "unknown kn_convention");
+
+    lb_handle* h = new (std::nothrow) lb_handle();
+    if (!h) return reject(LB_ERR_NOMEM, "host allocation");
+    h->p = P;
+    std::string err;
+    if (!lbh::build_velocity_set(P.quadrature, &h->vs, &err)) {
+        delete h;
+        return reject(LB_ERR_ARG, err);
+    }
+    if (h->vs.degree < P.n_eq + 2) {
+        delete h;
+        return reject(LB_ERR_UNSUPPORTED, "quadrature degree < N + 2: rho, u and T would not be conserved");
+    }
+    h->launch = pick_launcher(P.quadrature, P.precision);
+    if (!h->launch) {
+        delete h;
+        return reject(LB_ERR_UNSUPPORTED, "16-bit storage is built for the Gauss-Hermite product sets only");
+    }
+    h->dx = 2.0 * M_PI / P.nx;
+    double amax = 0;
+    for (double a : h->vs.axis) amax = std::max(amax, std::fabs(a));
+    h->dt = h->vs.on_lattice ? h->dx / h->vs.c : P.cfl * h->dx / amax;
+    h->tau = (P.kn_convention == LB_KN_LAMBDA) ? P.kn * std::sqrt(2.0 / M_PI) : P.kn;
+    h->omega = h->dt / (h->tau + 0.5 * h->dt);
+    h->V = lbk::cells_per_thread(h->vs.q);
+    const int tw = 32 * h->V;
+    h->pitch = (P.nx + 63) / 64 * 64;
+    h->plane = (long long)h->pitch * P.ny;
+    h->ncell = (long long)P.nx * P.ny;
+    h->ntiles_x = (P.nx + tw - 1) / tw;
+    h->ntiles = h->ntiles_x * ((P.ny + lbk::kRows - 1) / lbk::kRows);
+    h->pop_bytes = (size_t)h->vs.q * h->plane * storage_bytes(P.precision);
+
+    cudaError_t e;
+    if (P.stream) {
+        h->stream = static_cast<cudaStream_t>(P.stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            delete h;
+            return reject(LB_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    const int nsm = sm_count();
+    if (nsm <= 0) {
+        h->release();
+        delete h;
+        return reject(LB_ERR_CUDA, "no CUDA device");
+    }
+    int occ = 0;
+    {
+        lbk::Launch L{};
+        L.kind = -1;
+        L.n_eq = P.n_eq;
+        L.prec = P.precision;
+        L.args = &occ;
+        if (h->launch(L) != cudaSuccess || occ < 1) occ = 1;
+    }
+    h->grid = std::max(1, std::min(h->ntiles, nsm * occ));
+    h->grid_init = (int)std::max<long long>(1, std::min<long long>((h->ncell + lbk::kThreads - 1) / lbk::kThreads, 4LL * nsm));
+    const size_t rbytes = P.precision == LB_F64 ? 8 : 4;
+    h->buf[0] = h->dalloc(h->pop_bytes);
+    h->buf[1] = h->dalloc(h->pop_bytes);
+    h->sin_d = h->dalloc(rbytes * P.nx);
+    h->cos_d = h->dalloc(rbytes * P.nx);
+    h->partials = static_cast<double*>(h->dalloc(sizeof(double) * lbk::kDiagSlots * (size_t)h->grid));
+    h->ticket = static_cast<unsigned int*>(h->dalloc(256));
+    h->level_d = static_cast<long long*>(h->dalloc(256));
+    h->status = static_cast<int*>(h->dalloc(256));
+    h->ring = static_cast<lb_diag*>(h->dalloc(sizeof(lb_diag) * (size_t)P.diag_capacity));
+    if (!h->buf[0] || !h->buf[1] || !h->sin_d || !h->cos_d || !h->partials || !h->ticket || !h->level_d ||
+        !h->status || !h->ring) {
+        h->release();
+        delete h;
+        return reject(LB_ERR_NOMEM, "device allocation failed");
+    }
+    std::vector<double> sd(P.nx), cd(P.nx);
+    for (int i = 0; i < P.nx; ++i) {
+        sd[i] = std::sin(2.0 * M_PI * i / P.nx);
+        cd[i] = std::cos(2.0 * M_PI * i / P.nx);
+    }
+    if (P.precision == LB_F64) {
+        e = cudaMemcpyAsync(h->sin_d, sd.data(), 8 * P.nx, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->cos_d, cd.data(), 8 * P.nx, cudaMemcpyHostToDevice, h->stream);
+    } else {
+        std::vector<float> sf(sd.begin(), sd.end()), cf(cd.begin(), cd.end());
+        e = cudaMemcpyAsync(h->sin_d, sf.data(), 4 * P.nx, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->cos_d, cf.data(), 4 * P.nx, cudaMemcpyHostToDevice, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 256, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->release();
+        delete h;
+        return reject(LB_ERR_CUDA, std::string("setup copies: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_handle* h) {
+    if (!h) return LB_OK;
+    h->release();
+    delete h;
+    return LB_OK;
+}
+
+lb_status lb_init_shear_wave(lb_handle* h, double u0, double u1) {
+    if (!h) return LB_ERR_ARG;
+    if (!std::isfinite(u0) || !std::isfinite(u1)) return h->fail(LB_ERR_ARG, "non-finite amplitude");
+    set_scale_and_tables(h, std::fabs(u0) + std::fabs(u1));
+    return init_common(h, u0, u1, nullptr, nullptr, nullptr, nullptr);
+}
+
+lb_status lb_init_fields(lb_handle* h, const double* rho, const double* ux, const double* uy, const double* T) {
+    if (!h || !rho || !ux || !uy) return h ? h->fail(LB_ERR_ARG, "rho, ux, uy are required") : LB_ERR_ARG;
+    const size_t n = (size_t)h->ncell;
+    double amp = 0;
+    for (size_t i = 0; i < n; ++i) amp = std::max(amp, std::max(std::fabs(ux[i]), std::fabs(uy[i])));
+    set_scale_and_tables(h, amp);
+    if (!h->mom) {
+        h->mom = static_cast<double*>(h->dalloc(sizeof(double) * 5 * n));
+        if (!h->mom) return h->fail(LB_ERR_NOMEM, "moments scratch");
+    }
+    double* d = h->mom;
+    cudaError_t e = cudaMemcpyAsync(d, rho, 8 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, ux, 8 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * n, uy, 8 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && T) e = cudaMemcpyAsync(d + 3 * n, T, 8 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "initial fields upload");
+    lb_status st = init_common(h, 0, 0, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr);
+    if (st != LB_OK) return st;
+    e = cudaStreamSynchronize(h->stream);  // host arrays may be released by the caller
+    return e == cudaSuccess ? LB_OK : h->cuda_fail(e, "init sync");
+}
+
+lb_status lb_step(lb_handle* h, int n) {
+    if (!h || n < 0) return h ? h->fail(LB_ERR_ARG, "n must be >= 0") : LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_step before an init call");
+    lb_status st;
+    while (n > 0) {
+        cudaGraphExec_t* g = nullptr;
+        int len = 0;
+        if (n >= kChunk) {
+            g = &h->chunk[h->cur];
+            len = kChunk;
+        } else if (n >= 2) {
+            g = &h->pair[h->cur];
+            len = 2;
+        }
+        if (g) {
+            if (!*g && (st = build_graph(h, h->cur, len, g)) != LB_OK) return st;
+            const cudaError_t e = cudaGraphLaunch(*g, h->stream);
+            if (e != cudaSuccess) return h->cuda_fail(e, "cudaGraphLaunch");
+            h->launches += len;
+        } else {
+            len = 1;
+            if ((st = step_once(h, h->cur)) != LB_OK) return st;
+        }
+        // len is even for graphs: cur returns to itself; odd single step flips it
+        if (len & 1) h->cur = 1 - h->cur;
+        h->level += len;
+        h->raw_prev = false;
+        n -= len;
+    }
+    return LB_OK;
+}
+
+lb_status lb_synchronize(lb_handle* h) {
+    if (!h) return LB_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamSynchronize");
+    int status = 0;
+    e = cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return h->cuda_fail(e, "status read");
+    if (status & 1) return h->fail(LB_ERR_UNSTABLE, "the state became non-finite");
+    return LB_OK;
+}
+
+lb_status lb_moments_device(lb_handle* h, double* rho, double* ux, double* uy, double* T, double* sxy) {
+    if (!h) return LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_moments before an init call");
+    // the state f~(n) = stream(buffer read by the last launch)
+    const int prev = 1 - h->cur;
+    return launch_any(h, lbk::kMoments, h->buf[prev], nullptr, h->raw_prev ? 1 : 0, h->grid, rho, ux, uy, T, sxy,
+                      nullptr);
+}
+
+lb_status lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* T, double* sxy) {
+    if (!h) return LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_moments before an init call");
+    const size_t n = (size_t)h->ncell;
+    if (!h->mom) {
+        h->mom = static_cast<double*>(h->dalloc(sizeof(double) * 5 * n));
+        if (!h->mom) return h->fail(LB_ERR_NOMEM, "moments scratch");
+    }
+    double* d = h->mom;
+    lb_status st = lb_moments_device(h, rho ? d : nullptr, ux ? d + n : nullptr, uy ? d + 2 * n : nullptr,
+                                      T ? d + 3 * n : nullptr, sxy ? d + 4 * n : nullptr);
+    if (st != LB_OK) return st;
+    double* outs[5] = {rho, ux, uy, T, sxy};
+    for (int k = 0; k < 5; ++k) {
+        if (!outs[k]) continue;
+        const cudaError_t e = cudaMemcpyAsync(outs[k], d + k * n, 8 * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return h->cuda_fail(e, "moments read-back");
+    }
+    return lb_synchronize(h);
+}
+
+lb_status lb_populations(lb_handle* h, double* f) {
+    if (!h || !f) return h ? h->fail(LB_ERR_ARG, "null output") : LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_populations before an init call");
+    const size_t n = (size_t)h->ncell * h->vs.q;
+    if (!h->pop) {
+        h->pop = static_cast<double*>(h->dalloc(sizeof(double) * n));
+        if (!h->pop) return h->fail(LB_ERR_NOMEM, "population scratch");
+    }
+    const int prev = 1 - h->cur;
+    lb_status st = launch_any(h, lbk::kMoments, h->buf[prev], nullptr, h->raw_prev ? 1 : 0, h->grid, nullptr,
+                              nullptr, nullptr, nullptr, nullptr, h->pop);
+    if (st != LB_OK) return st;
+    const cudaError_t e = cudaMemcpyAsync(f, h->pop, 8 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "population read-back");
+    return lb_synchronize(h);
+}
+
+lb_status lb_diagnostics(lb_handle* h, lb_diag* out, int max_records, int* n_out) {
+    if (!h || !out || !n_out || max_records < 0) return h ? h->fail(LB_ERR_ARG, "bad arguments") : LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_diagnostics before an init call");
+    lb_status st = lb_synchronize(h);
+    if (st != LB_OK && st != LB_ERR_UNSTABLE) return st;
+    const long long total = h->level + 1;  // records for levels 0..n
+    const long long cap = h->p.diag_capacity;
+    const long long cnt = std::min<long long>(std::min(total, cap), max_records);
+    const long long first = total - cnt;
+    for (long long i = 0; i < cnt;) {
+        const long long slot = (first + i) % cap;
+        const long long run = std::min(cnt - i, cap - slot);
+        const cudaError_t e = cudaMemcpy(out + i, h->ring + slot, sizeof(lb_diag) * run, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return h->cuda_fail(e, "diagnostics read-back");
+        i += run;
+    }
+    *n_out = (int)cnt;
+    return st;
+}
+
+lb_status lb_get_info(const lb_handle* h, lb_info_t* o) {
+    if (!h || !o) return LB_ERR_ARG;
+    o->q = h->vs.q;
+    o->degree = h->vs.degree;
+    o->on_lattice = h->vs.on_lattice ? 1 : 0;
+    o->halo = h->vs.halo;
+    o->dx = h->dx;
+    o->dt = h->dt;
+    o->tau = h->tau;
+    o->omega = h->omega;
+    o->c_lattice = h->vs.c;
+    o->time_level = h->level;
+    o->records = h->initialized ? h->level + 1 : 0;
+    o->bytes_per_cell_update = 2 * (size_t)h->vs.q * storage_bytes(h->p.precision);
+    o->device_bytes = h->device_bytes;
+    o->storage_scale = h->scale;
+    return LB_OK;
+}
+
+long long lb_kernel_launches(const lb_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""Object wrapper around one liblb.so handle (marshalling only)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi
+
+
+class Lattice:
+    """One periodic nx x ny lattice advanced by the fused collide-stream kernels.
+
+    quadrature: "D2Q16-GH", "D2Q36-GH", "D2Q64-GH" (Lax-Wendroff streaming) or
+    "D2Q37", "D2Q9", "D2Q16-int", "D2Q17", "D2Q21", "D2Q25" (exact shift).
+    precision: "f32" (default), "f64", "bf16", "f16" (16-bit: GH sets only).
+    stream: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
+    or None for a stream the handle creates.
+    """
+
+    def __init__(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, precision: str = "f32",
+                 kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
+                 diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None):
+        p = capi.lb_params_default()
+        p.quadrature = capi.QUADRATURES[quadrature]
+        p.n_eq, p.nx, p.ny, p.kn = n_eq, nx, ny, kn
+        p.precision = capi.PRECISIONS[precision]
+        p.kn_convention = capi.KN_LAMBDA if kn_convention == "lambda" else capi.KN_PAPER
+        p.cfl = cfl
+        p.isothermal = int(isothermal)
+        p.diag_capacity = diag_capacity
+        p.storage_scale = storage_scale
+        p.stream = stream
+        self.quadrature, self.n_eq, self.nx, self.ny = quadrature, n_eq, nx, ny
+        self.h = capi.lb_create_ex(p)
+        inf = capi.lb_get_info(self.h)
+        self.Q = inf.q
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            capi.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def init_shear_wave(self, u0: float, u1: float = 0.0):
+        capi.lb_init_shear_wave(self.h, u0, u1)
+        return self
+
+    def init_fields(self, rho, ux, uy, T=None):
+        f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        capi.lb_init_fields(self.h, f(rho), f(ux), f(uy), f(T))
+        return self
+
+    def step(self, n: int = 1):
+        capi.lb_step(self.h, n)
+        return self
+
+    def synchronize(self):
+        capi.lb_synchronize(self.h)
+
+    def moments(self) -> dict:
+        out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T", "sxy")}
+        capi.lb_moments(self.h, *(out[k] for k in ("rho", "ux", "uy", "T", "sxy")))
+        return out
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((self.Q, self.ny, self.nx))
+        capi.lb_populations(self.h, f)
+        return f
+
+    def diagnostics(self, max_records: int | None = None) -> np.ndarray:
+        inf = capi.lb_get_info(self.h)
+        n = int(inf.records) if max_records is None else max_records
+        return capi.lb_diagnostics(self.h, max(n, 1))
+
+    @property
+    def info(self) -> dict:
+        inf = capi.lb_get_info(self.h)
+        return {k: getattr(inf, k) for k, _ in capi.lb_info_t._fields_}
+
+    @property
+    def launches(self) -> int:
+        return capi.lb_kernel_launches(self.h)

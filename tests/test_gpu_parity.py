@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances:
+* FP64 storage and arithmetic: the same algorithm in a different order of
+  rounding; populations agree to 1e-11 relative L2 of the deviation f - w.
+* FP32: within 1e-6 relative L2 of u_y and sigma_xy (the stated bound for the
+  FP32 collide-stream), on runs of <= 100 steps.
+Grids span several tiles with ragged tails in both directions (tile = 8 rows
+x 64 columns, or 32 columns for D2Q64-GH).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from lbtest import lib, order_map, rel_l2, run_both
+
+pytestmark = pytest.mark.gpu
+
+SETS_N = [("D2Q16-GH", 2), ("D2Q36-GH", 3), ("D2Q64-GH", 4), ("D2Q37", 3), ("D2Q9", 2),
+          ("D2Q16-int", 3), ("D2Q17", 4), ("D2Q21", 3), ("D2Q25", 4)]
+
+
+@pytest.mark.parametrize("quad,N", SETS_N)
+def test_f64_populations_match_oracle(quad, N):
+    L, P, f, d, capi = run_both(quad, N, 100, 11, 0.3, "f64", 25, u0=2e-2, u1=1e-2)
+    g = L.populations()
+    perm = order_map(capi, quad, P)
+    w = P.vs.w[perm][:, None, None]
+    dev_g = g - w
+    dev_o = f[perm] - w
+    assert rel_l2(dev_g, dev_o) < 1e-11
+    rec = L.diagnostics()
+    assert len(rec) == 26
+    np.testing.assert_allclose(rec["t"], d[:, 0], rtol=1e-13)
+    assert np.max(np.abs(rec["amp"] - d[:, 4])) < 1e-12 * np.max(np.abs(d[:, 4]))
+    assert np.max(np.abs(rec["shear"] - d[:, 5])) < 1e-11 * np.max(np.abs(d[:, 5]))
+    assert np.max(np.abs(rec["mass"] - d[:, 1])) < 1e-12 * d[0, 1]
+    assert np.max(np.abs(rec["hnorm"] - d[:, 6])) < 1e-10 * np.max(d[:, 6])
+
+
+@pytest.mark.parametrize("quad,N", SETS_N)
+def test_f32_moments_match_oracle(quad, N):
+    L, P, f, d, capi = run_both(quad, N, 100, 11, 0.3, "f32", 60, u0=1e-3, u1=1e-3)
+    m = L.moments()
+    o = P.moments(f)
+    assert rel_l2(m["uy"], o["uy"]) < 1e-6
+    assert rel_l2(m["sxy"], o["sxy"]) < 1e-6
+    assert np.max(np.abs(m["rho"] - o["rho"])) < 1e-7
+    rec = L.diagnostics()
+    assert np.max(np.abs(rec["amp"] - d[:, 4])) < 1e-6 * np.max(np.abs(d[:, 4]))
+
+
+@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 2, 1), ("D2Q37", 2, 2, 1), ("D2Q25", 3, 6, 3),
+                                          ("D2Q64-GH", 2, 34, 9), ("D2Q9", 2, 130, 17),
+                                          ("D2Q16-GH", 4, 64, 1)])
+def test_f64_edge_shapes(quad, N, nx, ny):
+    L, P, f, d, capi = run_both(quad, N, nx, ny, 0.2, "f64", 12, u0=1e-2, u1=5e-3)
+    perm = order_map(capi, quad, P)
+    w = P.vs.w[perm][:, None, None]
+    assert rel_l2(L.populations() - w, f[perm] - w) < 1e-11
+
+
+def test_isothermal_and_paper_convention():
+    Lattice, capi = lib()
+    L = Lattice("D2Q36-GH", 3, 64, 4, 0.5, precision="f64", isothermal=True, kn_convention="paper")
+    L.init_shear_wave(1e-2)
+    L.step(20)
+    P = oracle.Problem("D2Q36-GH", 3, 64, 4, 0.5, kn_convention="paper", isothermal=True)
+    f = P.init_shear(1e-2)
+    P.run(f, 20)
+    assert rel_l2(L.populations() - P.vs.w[:, None, None], f - P.vs.w[:, None, None]) < 1e-11
+
+
+def test_cfl_below_one():
+    Lattice, capi = lib()
+    L = Lattice("D2Q16-GH", 2, 64, 3, 0.1, precision="f64", cfl=0.6)
+    L.init_shear_wave(1e-2)
+    L.step(15)
+    P = oracle.Problem("D2Q16-GH", 2, 64, 3, 0.1, cfl=0.6)
+    f = P.init_shear(1e-2)
+    P.run(f, 15)
+    assert rel_l2(L.populations() - P.vs.w[:, None, None], f - P.vs.w[:, None, None]) < 1e-11
+    assert abs(L.info["dt"] - P.dt) < 1e-15
+
+
+def test_plain_small_full_run():
+    """The 64 x 1 D2Q16-GH FP64 run, 5000 steps, amplitude and shear every step."""
+    from paper_0908_4520_gb300 import inputs
+
+    c = inputs.plain_small()
+    L, P, f, d, capi = run_both(c["quadrature"], c["n_eq"], c["nx"], c["ny"], c["kn"], c["precision"],
+                                c["steps"], u0=c["u0"])
+    rec = L.diagnostics()
+    assert len(rec) == c["steps"] + 1
+    assert np.max(np.abs(rec["amp"] - d[:, 4])) < 1e-12 * c["u0"]
+    assert np.max(np.abs(rec["shear"] - d[:, 5])) < 1e-11 * np.max(np.abs(d[:, 5]))
+
+
+def test_step_splitting_is_bitwise():
+    Lattice, capi = lib()
+    a = Lattice("D2Q36-GH", 3, 96, 10, 0.1).init_shear_wave(1e-3, 1e-3)
+    b = Lattice("D2Q36-GH", 3, 96, 10, 0.1).init_shear_wave(1e-3, 1e-3)
+    a.step(77)
+    for n in (1, 2, 33, 5, 0, 36):
+        b.step(n)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    np.testing.assert_array_equal(a.diagnostics()["amp"], b.diagnostics()["amp"])
+    assert a.info["time_level"] == 77 and b.info["time_level"] == 77
+
+
+def test_diagnostics_ring_wraps():
+    Lattice, capi = lib()
+    L = Lattice("D2Q9", 2, 64, 2, 0.1, diag_capacity=16).init_shear_wave(1e-3)
+    L.step(40)
+    rec = L.diagnostics()
+    assert len(rec) == 16
+    dt = L.info["dt"]
+    np.testing.assert_allclose(rec["t"], dt * np.arange(25, 41), rtol=1e-12)
+
+
+def test_init_fields_equals_shear_wave():
+    Lattice, capi = lib()
+    nx, ny = 64, 8
+    x = 2 * np.pi * np.arange(nx) / nx
+    y = 2 * np.pi * np.arange(ny) / ny
+    uy = 1e-3 * np.sin(x)[None, :] + 2e-3 * np.sin(y)[:, None] * np.sin(x)[None, :]
+    a = Lattice("D2Q37", 3, nx, ny, 0.2, precision="f64").init_shear_wave(1e-3, 2e-3)
+    b = Lattice("D2Q37", 3, nx, ny, 0.2, precision="f64").init_fields(np.ones((ny, nx)), np.zeros((ny, nx)), uy)
+    np.testing.assert_allclose(a.populations(), b.populations(), rtol=1e-14, atol=1e-18)
+
+
+def test_error_states():
+    Lattice, capi = lib()
+    L = Lattice("D2Q9", 2, 16, 1, 0.1)
+    with pytest.raises(capi.LBError) as e:
+        L.step(1)
+    assert e.value.status == capi.LB_ERR_STATE
+    L.init_shear_wave(1e-3)
+    with pytest.raises(capi.LBError):
+        L.step(-1)
+    L.step(0)
+    assert L.info["time_level"] == 0
+
+
+def test_launch_count():
+    Lattice, capi = lib()
+    L = Lattice("D2Q16-GH", 2, 64, 1, 0.1).init_shear_wave(1e-3)
+    n0 = L.launches
+    L.step(70)
+    assert L.launches - n0 == 70
+
+
+@pytest.mark.parametrize("quad", ["D2Q36-GH", "D2Q37"])
+def test_full_size_rows_match_oracle(quad):
+    """4096 x 4096, N = 3, FP32, in the benchmark's launch configuration.  With u1 = 0 the
+    solution does not depend on y, so every row must equal the oracle's 4096 x 1 run."""
+    Lattice, capi = lib()
+    L = Lattice(quad, 3, 4096, 4096, 0.1).init_shear_wave(1e-3, 0.0)
+    L.step(12)
+    m = L.moments()
+    P = oracle.Problem(quad, 3, 4096, 1, 0.1)
+    f = P.init_shear(1e-3)
+    P.run(f, 12, record=False)
+    o = P.moments(f)
+    for row in range(0, 4096, 511):
+        assert rel_l2(m["uy"][row], o["uy"][0]) < 1e-6
+        assert rel_l2(m["sxy"][row], o["sxy"][0]) < 1e-6
+    L.close()
+
+
+def test_full_size_conservation():
+    """The benchmark workload itself (u1 != 0): FP64 grid sums stay conserved."""
+    Lattice, capi = lib()
+    L = Lattice("D2Q36-GH", 3, 4096, 4096, 0.1).init_shear_wave(1e-3, 1e-3)
+    L.step(8)
+    rec = L.diagnostics()
+    ncell = 4096.0 * 4096.0
+    # FP32 per-cell sums rounded independently: drift of order sqrt(ncell) * 1e-10
+    assert np.max(np.abs(rec["mass"] - ncell)) < 1e-3
+    assert np.max(np.abs(rec["mom_x"])) < 1e-3
+    assert np.max(np.abs(rec["mom_y"])) < 1e-3
+    assert np.all(rec["flags"] == 0)
+    L.close()
