@@ -46,7 +46,7 @@ typedef enum {
     LB_ERR_NOMEM = -3,        /* device or host allocation failed */
     LB_ERR_CUDA = -4,         /* CUDA runtime error (message in lb_last_error) */
     LB_ERR_UNSTABLE = -5,     /* the state became non-finite */
-    LB_ERR_TIMEOUT = -6,      /* a bounded device wait ran out */
+    LB_ERR_TIMEOUT = -6,      /* a bounded device wait ran out (the kernel stopped early) */
     LB_ERR_BUDGET = -7,       /* request exceeds the configured device-memory budget */
     LB_ERR_STATE = -8         /* call out of order (e.g. lb_step before an init) */
 } lb_status;
@@ -89,6 +89,9 @@ typedef struct {
     int isothermal;            /* 1: T = 1 in the equilibrium (default 0: kinetic T) */
     int diag_capacity;         /* records kept in the device ring (default 65536) */
     double storage_scale;      /* 16-bit scale S; 0 = set at init from the amplitude */
+    int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel
+                                  (LB_ERR_UNSUPPORTED if not built for the storage).  Both give
+                                  bitwise-identical results. */
     void *stream;              /* cudaStream_t to run on; NULL = a stream the handle creates */
     /* optional device allocator (e.g. PyTorch's caching allocator); both or neither */
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
@@ -113,6 +116,7 @@ typedef struct {
     double dx, dt, tau, omega;
     double c_lattice;   /* xi = c e for on-lattice sets, else 0 */
     long long time_level;   /* n: the state is f~(n dt) */
+    int tma_staged;         /* 1: steps run the TMA-staged kernel */
     long long records;      /* diagnostics records produced so far (n + 1 after init) */
     size_t bytes_per_cell_update; /* algorithmic HBM bytes: 2 q sizeof(storage) */
     size_t device_bytes;    /* device memory held by the handle */

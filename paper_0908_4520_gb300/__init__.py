@@ -12,7 +12,7 @@ __all__ = ["Lattice", "capi", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
 
     return _b(force=force)
 

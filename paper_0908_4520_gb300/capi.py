@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblb.so")
+LIB_PATH = os.environ.get("LB_LIB_PATH") or os.path.join(_PKG, "liblb.so")
 
 # lb_status
 LB_OK, LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_NOMEM, LB_ERR_CUDA = 0, -1, -2, -3, -4
@@ -37,7 +37,7 @@ class lb_params(ctypes.Structure):
         ("quadrature", ctypes.c_int), ("n_eq", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("kn", ctypes.c_double), ("precision", ctypes.c_int), ("kn_convention", ctypes.c_int),
         ("cfl", ctypes.c_double), ("isothermal", ctypes.c_int), ("diag_capacity", ctypes.c_int),
-        ("storage_scale", ctypes.c_double), ("stream", ctypes.c_void_p),
+        ("storage_scale", ctypes.c_double), ("step_kernel", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -53,7 +53,8 @@ class lb_info_t(ctypes.Structure):
     _fields_ = [
         ("q", ctypes.c_int), ("degree", ctypes.c_int), ("on_lattice", ctypes.c_int), ("halo", ctypes.c_int),
         ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double),
-        ("c_lattice", ctypes.c_double), ("time_level", ctypes.c_longlong), ("records", ctypes.c_longlong),
+        ("c_lattice", ctypes.c_double), ("time_level", ctypes.c_longlong), ("tma_staged", ctypes.c_int),
+        ("records", ctypes.c_longlong),
         ("bytes_per_cell_update", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
         ("storage_scale", ctypes.c_double),
     ]

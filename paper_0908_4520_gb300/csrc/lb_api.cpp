@@ -17,62 +17,38 @@
 #include "lb_host.h"
 
 namespace lbk {
-#define LB_DECL(set) \
-    cudaError_t launch_##set##_f32(const Launch&); \
-    cudaError_t launch_##set##_f64(const Launch&);
-#define LB_DECL16(set) \
-    LB_DECL(set)       \
-    cudaError_t launch_##set##_bf16(const Launch&); \
-    cudaError_t launch_##set##_f16(const Launch&);
-LB_DECL16(gh4)
-LB_DECL16(gh6)
-LB_DECL16(gh8)
-LB_DECL(d2q37)
-LB_DECL(d2q9)
-LB_DECL(d2q16i)
-LB_DECL(d2q17)
-LB_DECL(d2q21)
-LB_DECL(d2q25)
-#undef LB_DECL
-#undef LB_DECL16
+
+namespace {
+struct Registry {
+    std::mutex mu;
+    LaunchFn fn[16][4] = {};
+};
+Registry& registry() {
+    static Registry r;
+    return r;
+}
+}  // namespace
+
+bool register_launcher(int quadrature, int precision, LaunchFn fn) {
+    if (quadrature < 0 || quadrature >= 16 || precision < 0 || precision >= 4) return false;
+    Registry& r = registry();
+    std::lock_guard<std::mutex> g(r.mu);
+    r.fn[quadrature][precision] = fn;
+    return true;
+}
+
+LaunchFn find_launcher(int quadrature, int precision) {
+    if (quadrature < 0 || quadrature >= 16 || precision < 0 || precision >= 4) return nullptr;
+    Registry& r = registry();
+    std::lock_guard<std::mutex> g(r.mu);
+    return r.fn[quadrature][precision];
+}
+
 }  // namespace lbk
 
 namespace {
 
-using LaunchFn = cudaError_t (*)(const lbk::Launch&);
-
-LaunchFn pick_launcher(lb_quadrature q, lb_precision p) {
-#define LB_CASE(Q, set)                                      \
-    case Q:                                                  \
-        switch (p) {                                         \
-            case LB_F32: return lbk::launch_##set##_f32;     \
-            case LB_F64: return lbk::launch_##set##_f64;     \
-            default: return nullptr;                         \
-        }
-#define LB_CASE16(Q, set)                                    \
-    case Q:                                                  \
-        switch (p) {                                         \
-            case LB_F32: return lbk::launch_##set##_f32;     \
-            case LB_F64: return lbk::launch_##set##_f64;     \
-            case LB_BF16: return lbk::launch_##set##_bf16;   \
-            case LB_F16: return lbk::launch_##set##_f16;     \
-            default: return nullptr;                         \
-        }
-    switch (q) {
-        LB_CASE16(LB_D2Q16_GH, gh4)
-        LB_CASE16(LB_D2Q36_GH, gh6)
-        LB_CASE16(LB_D2Q64_GH, gh8)
-        LB_CASE(LB_D2Q37, d2q37)
-        LB_CASE(LB_D2Q9, d2q9)
-        LB_CASE(LB_D2Q16_INT, d2q16i)
-        LB_CASE(LB_D2Q17, d2q17)
-        LB_CASE(LB_D2Q21, d2q21)
-        LB_CASE(LB_D2Q25, d2q25)
-        default: return nullptr;
-    }
-#undef LB_CASE
-#undef LB_CASE16
-}
+using LaunchFn = lbk::LaunchFn;
 
 thread_local std::string g_create_error;
 
@@ -96,6 +72,25 @@ double hermite_he(int k, double x) {
     return h1;
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    });
+    return fn;
+}
+
 int sm_count() {
     static int n = 0;
     static std::once_flag once;
@@ -113,8 +108,12 @@ struct lb_handle {
     lb_params p{};
     lbh::VelocitySetInfo vs;
     LaunchFn launch = nullptr;
-    int V = 2, pitch = 0, ntiles_x = 0, ntiles = 0, grid = 0, grid_init = 0;
-    long long plane = 0, ncell = 0;
+    lbk::Shape shape{};
+    int pitch = 0, gy = 0, ntiles_x = 0, ntiles = 0, x0_last = 0, grid = 0, grid_init = 0;
+    bool use_tma = false;
+    int tma_ntiles_x = 0, tma_ntiles = 0, tma_x0_last = 0, tma_grid = 0;
+    CUtensorMap tmap[2];
+    long long plane = 0, origin = 0, ncell = 0;
     size_t pop_bytes = 0, device_bytes = 0;
     double dx = 0, dt = 0, tau = 0, omega = 0, scale = 1.0;
     cudaStream_t stream = nullptr;
@@ -175,14 +174,17 @@ struct lb_handle {
     }
 
     template <class R>
-    void fill_args(lbk::Args<R>& A) const {
+    void fill_args(lbk::Args<R>& A, bool tma) const {
         std::memset(&A, 0, sizeof(A));
         A.plane = plane;
+        A.origin = origin;
         A.nx = p.nx;
         A.ny = p.ny;
         A.pitch = pitch;
-        A.ntiles_x = ntiles_x;
-        A.ntiles = ntiles;
+        A.gy = gy;
+        A.ntiles_x = tma ? tma_ntiles_x : ntiles_x;
+        A.ntiles = tma ? tma_ntiles : ntiles;
+        A.x0_last = tma ? tma_x0_last : x0_last;
         A.isothermal = p.isothermal;
         A.diag_every = 1;
         A.omega = (R)omega;
@@ -230,7 +232,9 @@ lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int ra
                       double u0, double u1, const double* i_rho, const double* i_ux, const double* i_uy,
                       const double* i_T) {
     lbk::Args<R> A;
-    h->fill_args(A);
+    const bool tma = (kind == lbk::kStepTma);
+    h->fill_args(A, tma);
+    if (tma) A.tmap = h->tmap[src == h->buf[0] ? 0 : 1];
     A.src = src;
     A.dst = dst;
     A.raw = raw;
@@ -249,7 +253,6 @@ lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int ra
     lbk::Launch L;
     L.kind = kind;
     L.n_eq = h->p.n_eq;
-    L.prec = h->p.precision;
     L.grid = grid;
     L.stream = h->stream;
     L.args = &A;
@@ -274,7 +277,32 @@ lb_status launch_any(lb_handle* h, int kind, const void* src, void* dst, int raw
 
 // One step launch: level n -> n+1 (src = buf[cur] holds f*(n-1), dst gets f*(n)).
 lb_status step_once(lb_handle* h, int from) {
+    if (h->use_tma) return launch_any(h, lbk::kStepTma, h->buf[from], h->buf[1 - from], 0, h->tma_grid);
     return launch_any(h, lbk::kStep, h->buf[from], h->buf[1 - from], 0, h->grid);
+}
+
+lb_status encode_maps(lb_handle* h) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return h->fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    CUtensorMapDataType dt;
+    switch (h->p.precision) {
+        case LB_F32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+        case LB_BF16: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+        case LB_F16: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+        default: return h->fail(LB_ERR_UNSUPPORTED, "TMA staging is built for 32- and 16-bit storage");
+    }
+    const size_t b = storage_bytes(h->p.precision);
+    const cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->p.ny + 2 * h->gy), (cuuint64_t)h->vs.q};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->pitch * b, (cuuint64_t)h->plane * b};
+    const cuuint32_t box[3] = {(cuuint32_t)h->shape.box_w, (cuuint32_t)h->shape.box_h, (cuuint32_t)h->shape.box_d};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int i = 0; i < 2; ++i) {
+        const CUresult r = enc(&h->tmap[i], dt, 3, h->buf[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return h->fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    }
+    return LB_OK;
 }
 
 lb_status build_graph(lb_handle* h, int from, int nsteps, cudaGraphExec_t* out) {
@@ -358,6 +386,7 @@ void lb_params_default(lb_params* p) {
     p->isothermal = 0;
     p->diag_capacity = 65536;
     p->storage_scale = 0.0;
+    p->step_kernel = 0;
 }
 
 const char* lb_status_string(lb_status s) {
@@ -429,6 +458,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     if ((P.alloc == nullptr) != (P.free == nullptr)) return reject(LB_ERR_ARG, "alloc and free go together");
     if (P.kn_convention != LB_KN_LAMBDA && P.kn_convention != LB_KN_PAPER)
         return reject(LB_ERR_ARG, "unknown kn_convention");
+    if (P.step_kernel < 0 || P.step_kernel > 2) return reject(LB_ERR_ARG, "step_kernel must be 0, 1 or 2");
 
     lb_handle* h = new (std::nothrow) lb_handle();
     if (!h) return reject(LB_ERR_NOMEM, "host allocation");
@@ -442,10 +472,12 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         delete h;
         return reject(LB_ERR_UNSUPPORTED, "quadrature degree < N + 2: rho, u and T would not be conserved");
     }
-    h->launch = pick_launcher(P.quadrature, P.precision);
+    h->launch = lbk::find_launcher(P.quadrature, P.precision);
     if (!h->launch) {
         delete h;
-        return reject(LB_ERR_UNSUPPORTED, "16-bit storage is built for the Gauss-Hermite product sets only");
+        return reject(LB_ERR_UNSUPPORTED, (P.precision == LB_BF16 || P.precision == LB_F16)
+                                              ? "16-bit storage is built for the Gauss-Hermite product sets only"
+                                              : "this (quadrature, precision) unit is not in the build");
     }
     h->dx = 2.0 * M_PI / P.nx;
     double amax = 0;
@@ -453,13 +485,27 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     h->dt = h->vs.on_lattice ? h->dx / h->vs.c : P.cfl * h->dx / amax;
     h->tau = (P.kn_convention == LB_KN_LAMBDA) ? P.kn * std::sqrt(2.0 / M_PI) : P.kn;
     h->omega = h->dt / (h->tau + 0.5 * h->dt);
-    h->V = lbk::cells_per_thread(h->vs.q);
-    const int tw = 32 * h->V;
-    h->pitch = (P.nx + 63) / 64 * 64;
-    h->plane = (long long)h->pitch * P.ny;
+    {
+        lbk::Launch L{};
+        L.kind = lbk::kQueryShape;
+        L.n_eq = P.n_eq;
+        L.args = &h->shape;
+        if (h->launch(L) != cudaSuccess) {
+            h->shape.V = 1;
+            h->shape.rows = 8;
+            h->shape.threads = 256;
+            h->shape.occupancy = 0;
+        }
+    }
+    const int tw = 32 * h->shape.V;
+    h->gy = h->vs.halo;
+    h->pitch = (P.nx + 2 * lbk::kGhostX + 63) / 64 * 64;
+    h->plane = (long long)h->pitch * (P.ny + 2 * h->gy);
+    h->origin = (long long)h->gy * h->pitch + lbk::kGhostX;
     h->ncell = (long long)P.nx * P.ny;
     h->ntiles_x = (P.nx + tw - 1) / tw;
-    h->ntiles = h->ntiles_x * ((P.ny + lbk::kRows - 1) / lbk::kRows);
+    h->x0_last = P.nx >= tw ? P.nx - tw : 0;
+    h->ntiles = h->ntiles_x * ((P.ny + h->shape.rows - 1) / h->shape.rows);
     h->pop_bytes = (size_t)h->vs.q * h->plane * storage_bytes(P.precision);
 
     cudaError_t e;
@@ -478,23 +524,29 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         delete h;
         return reject(LB_ERR_CUDA, "no CUDA device");
     }
-    int occ = 0;
-    {
-        lbk::Launch L{};
-        L.kind = -1;
-        L.n_eq = P.n_eq;
-        L.prec = P.precision;
-        L.args = &occ;
-        if (h->launch(L) != cudaSuccess || occ < 1) occ = 1;
+    const int occ = std::max(1, h->shape.occupancy);
+    if (h->shape.tma) {
+        const int ttw = 32 * h->shape.tma_V;
+        h->tma_ntiles_x = (P.nx + ttw - 1) / ttw;
+        h->tma_x0_last = P.nx >= ttw ? P.nx - ttw : 0;
+        h->tma_ntiles = h->tma_ntiles_x * ((P.ny + h->shape.tma_rows - 1) / h->shape.tma_rows);
+        h->tma_grid = std::max(1, std::min(h->tma_ntiles, nsm * std::max(1, h->shape.tma_occupancy)));
+        // auto: TMA staging once the grid fills a tile row and every SM gets work
+        const bool big = P.nx >= ttw && h->tma_ntiles >= nsm;
+        h->use_tma = P.step_kernel == 2 || (P.step_kernel == 0 && big);
+    } else if (P.step_kernel == 2) {
+        delete h;
+        return reject(LB_ERR_UNSUPPORTED, "no TMA-staged step kernel for this storage");
     }
     h->grid = std::max(1, std::min(h->ntiles, nsm * occ));
-    h->grid_init = (int)std::max<long long>(1, std::min<long long>((h->ncell + lbk::kThreads - 1) / lbk::kThreads, 4LL * nsm));
+    h->grid_init = (int)std::max<long long>(1, std::min<long long>((h->ncell + 255) / 256, 4LL * nsm));
     const size_t rbytes = P.precision == LB_F64 ? 8 : 4;
     h->buf[0] = h->dalloc(h->pop_bytes);
     h->buf[1] = h->dalloc(h->pop_bytes);
     h->sin_d = h->dalloc(rbytes * P.nx);
     h->cos_d = h->dalloc(rbytes * P.nx);
-    h->partials = static_cast<double*>(h->dalloc(sizeof(double) * lbk::kDiagSlots * (size_t)h->grid));
+    h->partials = static_cast<double*>(
+        h->dalloc(sizeof(double) * lbk::kDiagSlots * (size_t)std::max(h->grid, h->tma_grid)));
     h->ticket = static_cast<unsigned int*>(h->dalloc(256));
     h->level_d = static_cast<long long*>(h->dalloc(256));
     h->status = static_cast<int*>(h->dalloc(256));
@@ -519,11 +571,22 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->cos_d, cf.data(), 4 * P.nx, cudaMemcpyHostToDevice, h->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 256, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, h->pop_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, h->pop_bytes, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         h->release();
         delete h;
         return reject(LB_ERR_CUDA, std::string("setup copies: ") + cudaGetErrorString(e));
+    }
+    if (h->use_tma) {
+        const lb_status st = encode_maps(h);
+        if (st != LB_OK) {
+            const std::string m = h->err;
+            h->release();
+            delete h;
+            return reject(st, m);
+        }
     }
     *out = h;
     return LB_OK;
@@ -604,6 +667,7 @@ lb_status lb_synchronize(lb_handle* h) {
     int status = 0;
     e = cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return h->cuda_fail(e, "status read");
+    if (status & 2) return h->fail(LB_ERR_TIMEOUT, "a bounded wait in the step kernel ran out");
     if (status & 1) return h->fail(LB_ERR_UNSTABLE, "the state became non-finite");
     return LB_OK;
 }
@@ -687,6 +751,7 @@ lb_status lb_get_info(const lb_handle* h, lb_info_t* o) {
     o->omega = h->omega;
     o->c_lattice = h->vs.c;
     o->time_level = h->level;
+    o->tma_staged = h->use_tma ? 1 : 0;
     o->records = h->initialized ? h->level + 1 : 0;
     o->bytes_per_cell_update = 2 * (size_t)h->vs.q * storage_bytes(h->p.precision);
     o->device_bytes = h->device_bytes;

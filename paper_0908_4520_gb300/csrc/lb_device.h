@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lb.h"
@@ -14,9 +15,8 @@ namespace lbk {
 constexpr int kMaxQ = lbvs::kMaxQ;
 constexpr int kMaxNA = lbvs::kMaxNA;
 constexpr int kMaxN = 4;
-constexpr int kRows = 8;             // warps per block = lattice rows per tile
-constexpr int kThreads = 32 * kRows; // threads per block
-constexpr int kDiagSlots = 8;        // doubles per partial / record
+constexpr int kDiagSlots = 8;  // doubles per partial / record
+constexpr int kGhostX = 8;     // ghost columns kept on each side of a population row
 
 // Per-handle constant tables, passed by value in the kernel parameter space
 // (constant bank): per-velocity entries are read with compile-time indices.
@@ -33,15 +33,23 @@ struct Tab {
     R scinv[kMaxQ];           // 16-bit storage: stored = deviation / (w S)
 };
 
-enum Kind : int { kStep = 0, kMoments = 1, kInit = 2 };
+enum Kind : int { kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kQueryShape = -1 };
 
+// Population layout: plane a, row y, column x at
+//   a * plane + origin + y * pitch + x,   origin = gy * pitch + kGhostX,
+// for -kGhostX <= x < nx + kGhostX and -gy <= y < ny + gy: the rim holds the
+// periodic images of the grid, rewritten by every launch that writes the
+// populations, so streaming never wraps an index.
 template <class R>
 struct Args {
+    CUtensorMap tmap;         // TMA view of src (step kernel with TMA staging only)
     const void* src;          // populations read (storage type), q planes
     void* dst;                // populations written
-    long long plane;          // elements per population plane (ny * pitch)
-    int nx, ny, pitch;
-    int ntiles_x, ntiles;     // tile grid (tile = kRows rows x 32*V columns)
+    long long plane;          // elements per population plane ((ny + 2 gy) * pitch)
+    long long origin;         // offset of cell (0, 0) in a plane
+    int nx, ny, pitch, gy;
+    int ntiles_x, ntiles;     // tile grid (tile = rows x 32*V columns)
+    int x0_last;              // first column of the last tile of a row (nx - 32V when nx >= 32V)
     int raw;                  // 1: src holds f~ itself (no streaming)
     int isothermal;
     int diag_every;           // record diagnostics when level % diag_every == 0
@@ -65,16 +73,30 @@ struct Args {
     Tab<R> tab;
 };
 
+// Launch geometry of a compiled (set, storage) unit.
+struct Shape {
+    int V;          // cells per thread along x (tile width 32 V), register kernels
+    int rows;       // warps per block = lattice rows per tile
+    int threads;    // 32 * rows
+    int occupancy;  // resident blocks per SM of the step kernel
+    // TMA-staged step kernel (0 = not built for this unit)
+    int tma;
+    int tma_V, tma_rows, tma_threads, tma_smem, tma_occupancy;
+    int box_w, box_h, box_d;  // tensor-map box (x, y, velocities)
+};
+
 struct Launch {
     int kind;                 // Kind
     int n_eq;                 // 2..4
-    lb_precision prec;
     int grid;                 // blocks (persistent grid-stride over tiles)
     cudaStream_t stream;
-    const void* args;         // Args<float> or Args<double> matching prec
+    const void* args;         // Args<float>/Args<double> matching the unit, or Shape* for kQueryShape
 };
 
-// Cells per thread along x for a set (the tile width is 32 * V).
-constexpr int cells_per_thread(int q) { return q > 40 ? 1 : 2; }
+using LaunchFn = cudaError_t (*)(const Launch&);
+
+// Every generated (set, storage) unit registers its entry point at load time.
+bool register_launcher(int quadrature, int precision, LaunchFn fn);
+LaunchFn find_launcher(int quadrature, int precision);
 
 }  // namespace lbk

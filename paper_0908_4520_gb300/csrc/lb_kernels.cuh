@@ -17,14 +17,29 @@
 // moments and equilibrium are formed without the O(1) background and keep
 // FP32 precision relative to the O(U0) signal.
 //
-// Work decomposition: a tile is kRows lattice rows x 32 V columns; warp w of a
+// Work decomposition: a tile is ROWS lattice rows x 32 V columns; warp w of a
 // block owns row y0 + w and each lane V consecutive cells, so every
 // population-plane access of a warp is one contiguous row segment (coalesced,
-// vectorised when V = 2).  The grid is persistent (a multiple of the SM count)
-// and walks tiles row-major, so the halo rows a tile re-reads were fetched
-// moments earlier by its neighbours and sit in L2.
+// vectorised when V = 2).  The last tile of a row is shifted left to end at
+// nx (its overlap with the previous tile is recomputed but neither stored nor
+// counted), so every warp of a row wider than a tile is full.  The grid is
+// persistent (a multiple of the SM count) and walks tiles row-major, so the
+// halo rows a tile re-reads were fetched moments earlier by its neighbours and
+// sit in L2.  Populations carry a rim of periodic images (ghost columns and
+// rows), rewritten by every store, so no read ever wraps.
+//
+// Two step kernels share the collision code and give bitwise-identical results:
+//  * lb_tma_step_kernel (the hot path): one producer warp streams, per group of
+//    velocities, the tile's source box (with its halo) from HBM into a ring of
+//    shared-memory stages with cp.async.bulk.tensor, completion tracked by
+//    mbarriers; the consumer warps read their row from shared memory, so the
+//    next tile's loads overlap this tile's collision.  Every wait is bounded:
+//    on expiry the kernel flags LB_ERR_TIMEOUT in the status word and returns.
+//  * lb_fused_kernel: plain coalesced loads from global memory (moments read-back,
+//    the first level, FP64 storage and grids too small for the TMA tiles).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -52,6 +67,41 @@ __device__ __forceinline__ R ld1(const S* p, R scale) {
         (void)scale;
         return __ldg(p);
     }
+}
+
+// shared-memory loads (plain, no read-only path)
+template <class S, class R>
+__device__ __forceinline__ R sld1(const S* p, R scale) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        return __bfloat162float(*p) * scale;
+    } else if constexpr (std::is_same<S, __half>::value) {
+        return __half2float(*p) * scale;
+    } else {
+        (void)scale;
+        return *p;
+    }
+}
+
+template <class S, class R>
+__device__ __forceinline__ void sld2(const S* p, R scale, R& v0, R& v1) {
+    if constexpr (std::is_same<S, float>::value) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v0 = t.x;
+        v1 = t.y;
+    } else if constexpr (std::is_same<S, double>::value) {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        v0 = t.x;
+        v1 = t.y;
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        v0 = t.x * scale;
+        v1 = t.y * scale;
+    } else {
+        const float2 t = __half22float2(*reinterpret_cast<const __half2*>(p));
+        v0 = t.x * scale;
+        v1 = t.y * scale;
+    }
+    (void)scale;
 }
 
 // aligned pair p[0], p[1]
@@ -92,13 +142,13 @@ __device__ __forceinline__ void st1(S* p, R v, R scinv) {
 template <class S, class R>
 __device__ __forceinline__ void st2(S* p, R v0, R v1, R scinv) {
     if constexpr (std::is_same<S, float>::value) {
-        *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
+        __stcs(reinterpret_cast<float2*>(p), make_float2(v0, v1));
     } else if constexpr (std::is_same<S, double>::value) {
-        *reinterpret_cast<double2*>(p) = make_double2(v0, v1);
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v0, v1));
     } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v0 * scinv, v1 * scinv);
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v0 * scinv, v1 * scinv));
     } else {
-        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v0 * scinv, v1 * scinv);
+        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v0 * scinv, v1 * scinv));
     }
     (void)scinv;
 }
@@ -119,11 +169,6 @@ __device__ __forceinline__ R store_scale(const Tab<R>& t, int a) {
     return R(1);
 }
 
-__device__ __forceinline__ int wrap_mod(int v, int n) {
-    int r = v % n;
-    return r < 0 ? r + n : r;
-}
-
 // compile-time loop: f(integral_constant<int, a>) for a in [A_, Q)
 template <int A_, int Q, class F>
 __device__ __forceinline__ void static_for(F&& f) {
@@ -133,11 +178,69 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// ------------------------------------------------------------ configuration
+// Register kernel: cells per thread, rows per block, min resident blocks.
+// TMA kernel: consumer rows, velocities per stage, shared-memory budget.
+// Overridable at build time for tuning sweeps.
+#ifndef LB_CFG_V
+#define LB_CFG_V 2
+#endif
+#ifndef LB_CFG_ROWS
+#define LB_CFG_ROWS 8
+#endif
+#ifndef LB_CFG_MINB
+#define LB_CFG_MINB 1
+#endif
+#ifndef LB_TMA_ROWS
+#define LB_TMA_ROWS 8
+#endif
+#ifndef LB_TMA_K
+#define LB_TMA_K 4
+#endif
+#ifndef LB_TMA_SMEM
+#define LB_TMA_SMEM (200 * 1024)
+#endif
+#ifndef LB_TMA_MINB
+#define LB_TMA_MINB 1
+#endif
+
+template <class VS, class S>
+struct Cfg {
+    static constexpr int V = (sizeof(S) == 8 || VS::Q > 40) ? 1 : LB_CFG_V;
+    static constexpr int ROWS = LB_CFG_ROWS;
+    static constexpr int THREADS = 32 * ROWS;
+    static constexpr int MINB = LB_CFG_MINB;
+};
+
+template <class VS, class S>
+struct TmaCfg {
+    static constexpr int V = (sizeof(S) == 8) ? 1 : 2;
+    static constexpr int ROWS = LB_TMA_ROWS;            // consumer warps
+    static constexpr int TW = 32 * V;
+    static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
+    static constexpr bool LW = !VS::kOnLattice;
+    static constexpr int BW = LW ? TW + 2 * AL : TW + AL;
+    static constexpr int BH = LW ? ROWS + 2 : ROWS;
+    static constexpr int BOX = BW * BH;                 // elements of one velocity's box
+    // stride of the velocity slots in a stage: dense for one 3-D box (Lax-Wendroff),
+    // 128-byte aligned for separate boxes (exact shift)
+    static constexpr int SLOT = LW ? BOX : ((BOX * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
+    static constexpr int K = LB_TMA_K;                  // velocities per stage
+    static constexpr int NG = (VS::Q + K - 1) / K;      // stages per tile
+    static constexpr int STAGE_BYTES = (K * SLOT * (int)sizeof(S) + 127) / 128 * 128;
+    static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
+    static constexpr int NS = NS_FIT < 2 * NG ? NS_FIT : 2 * NG;
+    static constexpr int THREADS = 32 * (ROWS + 1);     // + one producer warp
+    static constexpr int SMEM = NS * STAGE_BYTES + 2 * NS * 8 + 128;  // + alignment slack
+    static constexpr int BOX_D = LW ? K : 1;            // velocities per TMA box
+};
+
 // ------------------------------------------------------------ equilibrium
 // Deviation of the truncated Hermite equilibrium from w rho0, for one cell:
 // deq_a = w_a (drho + rho * sum'_{kx+ky<=N} c_kx(ux) c_ky(uy) hn[ix][kx] hn[iy][ky]),
-// sum' without the (0,0) term (which is rho itself).  emit(a, deq_a) is called for
-// every velocity with a compile-time a after unrolling.
+// sum' without the (0,0) term (which is rho itself).  The velocities are visited
+// grouped by their x axis node, so only one row of x partial sums is live.
+// emit(integral_constant<a>, deq_a) is called once per velocity.
 template <class VS, int N, class R, class Emit>
 __device__ __forceinline__ void equilibrium_dev(const Tab<R>& t, R drho, R rho, R ux, R uy, R th,
                                                 Emit&& emit) {
@@ -152,18 +255,6 @@ __device__ __forceinline__ void equilibrium_dev(const Tab<R>& t, R drho, R rho, 
         cx[k + 1] = ux * cx[k] + R(k) * th * cx[k - 1];
         cy[k + 1] = uy * cy[k] + R(k) * th * cy[k - 1];
     }
-    // px[i][0] excludes kx = 0; px[i][ky>=1] = sum_{kx <= N-ky} cx[kx] hn[i][kx]
-    R px[NA][N + 1];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) {
-#pragma unroll
-        for (int ky = 0; ky <= N; ++ky) {
-            R s = (ky == 0) ? R(0) : R(1);
-#pragma unroll
-            for (int kx = 1; kx <= N - ky; ++kx) s = fma(cx[kx], t.hn[i][kx], s);
-            px[i][ky] = s;
-        }
-    }
     R qy[NA][N + 1];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
@@ -171,107 +262,45 @@ __device__ __forceinline__ void equilibrium_dev(const Tab<R>& t, R drho, R rho, 
 #pragma unroll
         for (int ky = 1; ky <= N; ++ky) qy[j][ky] = cy[ky] * t.hn[j][ky];
     }
-    static_for<0, VS::Q>([&](auto ac) {
-        constexpr int a = decltype(ac)::value;
-        constexpr int ix = VS::ix(a), iy = VS::iy(a);
-        R s = px[ix][0];
+    static_for<0, NA>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        // px[0] excludes kx = 0; px[ky>=1] = sum_{kx <= N-ky} cx[kx] hn[I][kx]
+        R px[N + 1];
 #pragma unroll
-        for (int ky = 1; ky <= N; ++ky) s = fma(px[ix][ky], qy[iy][ky], s);
-        emit(ac, t.w[a] * fma(rho, s, drho));
+        for (int ky = 0; ky <= N; ++ky) {
+            R s = (ky == 0) ? R(0) : R(1);
+#pragma unroll
+            for (int kx = 1; kx <= N - ky; ++kx) s = fma(cx[kx], t.hn[I][kx], s);
+            px[ky] = s;
+        }
+        static_for<0, VS::Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (VS::ix(a) == I) {
+                constexpr int iy = VS::iy(a);
+                R s = px[0];
+#pragma unroll
+                for (int ky = 1; ky <= N; ++ky) s = fma(px[ky], qy[iy][ky], s);
+                emit(ac, t.w[a] * fma(rho, s, drho));
+            }
+        });
     });
 }
 
-// ------------------------------------------------------------ streaming
-// Pull-stream population a into v[0..V) for the cells (xl .. xl+V-1, y) of this lane.
-template <class VS, class S, class R, int V>
-struct Streamer {
-    static constexpr int TW = 32 * V;
-
-    // exact shift: f~_a(x, y) = f*_a(x - ex, y - ey)
-    template <int A_>
-    __device__ __forceinline__ static void shift(const Args<R>& A, const S* __restrict__ src, int y,
-                                                 bool interior, int xl, R (&v)[V]) {
-        constexpr int ex = VS::ex(A_), ey = VS::ey(A_);
-        const R sc = load_scale<S, R>(A.tab, A_);
-        int ys = y - ey;
-        if (A.ny >= VS::kHalo) {
-            ys = ys < 0 ? ys + A.ny : (ys >= A.ny ? ys - A.ny : ys);
-        } else {
-            ys = wrap_mod(ys, A.ny);
-        }
-        const S* row = src + (long long)A_ * A.plane + (long long)ys * A.pitch;
-        if (interior) {
-            const int xs = xl - ex;
-            if constexpr (V == 2 && (ex % 2 == 0)) {
-                ld2<S, R>(row + xs, sc, v[0], v[V - 1]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < V; ++k) v[k] = ld1<S, R>(row + xs + k, sc);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < V; ++k) v[k] = ld1<S, R>(row + wrap_mod(xl + k - ex, A.nx), sc);
-        }
-    }
-
-    // tensor-product Lax-Wendroff: y pass in registers, x pass through warp shuffles
-    template <int A_>
-    __device__ __forceinline__ static void laxw(const Args<R>& A, const S* __restrict__ src, int y,
-                                                int ym, int yp, int lane, int xl, R (&v)[V]) {
-        constexpr int ix = VS::ix(A_), iy = VS::iy(A_);
-        const R sc = load_scale<S, R>(A.tab, A_);
-        const R ly0 = A.tab.lw[iy][0], ly1 = A.tab.lw[iy][1], ly2 = A.tab.lw[iy][2];
-        const R lx0 = A.tab.lw[ix][0], lx1 = A.tab.lw[ix][1], lx2 = A.tab.lw[ix][2];
-        const S* base = src + (long long)A_ * A.plane;
-        const S* r0 = base + (long long)y * A.pitch;
-        const S* rm = base + (long long)ym * A.pitch;
-        const S* rp = base + (long long)yp * A.pitch;
-        const bool yflat = (A.ny == 1);
-        R g[V];
-        {
-            R f0[V], fm[V], fp[V];
-            if constexpr (V == 2) {
-                ld2<S, R>(r0 + xl, sc, f0[0], f0[1]);
-            } else {
-                f0[0] = ld1<S, R>(r0 + xl, sc);
-            }
-            if (yflat) {
-#pragma unroll
-                for (int k = 0; k < V; ++k) g[k] = f0[k];
-            } else {
-                if constexpr (V == 2) {
-                    ld2<S, R>(rm + xl, sc, fm[0], fm[1]);
-                    ld2<S, R>(rp + xl, sc, fp[0], fp[1]);
-                } else {
-                    fm[0] = ld1<S, R>(rm + xl, sc);
-                    fp[0] = ld1<S, R>(rp + xl, sc);
-                }
-#pragma unroll
-                for (int k = 0; k < V; ++k) g[k] = fma(ly0, fm[k], fma(ly1, f0[k], ly2 * fp[k]));
-            }
-        }
-        // neighbours of the lane's cells along x
-        R gl = __shfl_up_sync(0xffffffffu, g[V - 1], 1);
-        R gr = __shfl_down_sync(0xffffffffu, g[0], 1);
-        const bool needL = (lane == 0);
-        const bool needR = (lane == 31) || (xl + V >= A.nx);
-        if (needL || needR) {
-            auto column = [&](int xc) -> R {
-                const R c0 = ld1<S, R>(r0 + xc, sc);
-                if (yflat) return c0;
-                return fma(ly0, ld1<S, R>(rm + xc, sc), fma(ly1, c0, ly2 * ld1<S, R>(rp + xc, sc)));
-            };
-            if (needL) gl = column(wrap_mod(xl - 1, A.nx));
-            if (needR) gr = column(wrap_mod(xl + V, A.nx));
-        }
-        if constexpr (V == 2) {
-            v[0] = fma(lx0, gl, fma(lx1, g[0], lx2 * g[1]));
-            v[1] = fma(lx0, g[0], fma(lx1, g[1], lx2 * gr));
-        } else {
-            v[0] = fma(lx0, gl, fma(lx1, g[0], lx2 * gr));
-        }
-    }
+// ------------------------------------------------------------ tile geometry
+struct Lane {
+    int x;          // first cell of the lane
+    int xl;         // column read for the lane (x, or nx for lanes past the grid)
+    bool own;       // x < nx and not a recomputed overlap cell
 };
+
+template <int V>
+__device__ __forceinline__ Lane lane_geometry(int lane, int x0, int tile_start, int nx) {
+    Lane g;
+    g.x = x0 + lane * V;
+    g.own = g.x < nx && g.x >= tile_start;
+    g.xl = g.x < nx ? g.x : nx;  // the first column past the grid is a valid image
+    return g;
+}
 
 template <class R>
 __device__ __forceinline__ R warp_sum(R v) {
@@ -280,14 +309,201 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-// ------------------------------------------------------------ fused kernel
+// Write the lane's V values of plane `pl` (pointer to cell (0,0)) at (x, y) and at
+// every periodic image inside the ghost rim.
+template <class S, class R, int V>
+__device__ __forceinline__ void store_cells(const Args<R>& A, S* pl, int x, int y, const R (&v)[V], R si) {
+    S* p = pl + (long long)y * A.pitch + x;
+    if constexpr (V == 2) {
+        st2<S, R>(p, v[0], v[1], si);
+    } else {
+        st1<S, R>(p, v[0], si);
+    }
+    if (x < kGhostX || x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) {
+        int ylo = y;
+        while (ylo - A.ny >= -A.gy) ylo -= A.ny;
+        int xlo = x;
+        while (xlo - A.nx >= -kGhostX) xlo -= A.nx;
+        for (int yi = ylo; yi < A.ny + A.gy; yi += A.ny) {
+            for (int xi = xlo; xi + V <= A.nx + kGhostX; xi += A.nx) {
+                if (xi == x && yi == y) continue;
+                S* q = pl + (long long)yi * A.pitch + xi;
+                if constexpr (V == 2) {
+                    st2<S, R>(q, v[0], v[1], si);
+                } else {
+                    st1<S, R>(q, v[0], si);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ collision (shared)
+// Moments, equilibrium, relaxation and the store (or the moment outputs) of the
+// cells (g.x .. g.x+V-1, y) whose streamed populations are in ft.  Diagnostics
+// are reduced over the warp in FP32 and added to acc (lane 0) in FP64.
+template <class VS, int N, class S, class R, int V, int KIND>
+__device__ __forceinline__ void collide_store(const Args<R>& A, R (&ft)[VS::Q][V], S* __restrict__ dst, int y,
+                                              const Lane& g, bool diag, double (&acc)[6], int lane) {
+    constexpr int Q = VS::Q;
+    const R omega = A.omega;
+    R drho[V], jx[V], jy[V], en[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) drho[k] = jx[k] = jy[k] = en[k] = R(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const R ax = A.tab.a[VS::ix(a)], ay = A.tab.a[VS::iy(a)], a2 = A.tab.xi2[a];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            drho[k] += ft[a][k];
+            jx[k] = fma(ax, ft[a][k], jx[k]);
+            jy[k] = fma(ay, ft[a][k], jy[k]);
+            en[k] = fma(a2, ft[a][k], en[k]);
+        }
+    }
+    R sig[V], hh[V], uyv[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const R rho = A.rho0 + drho[k];
+        const R inv = R(1) / rho;
+        const R ux = jx[k] * inv, uy = jy[k] * inv;
+        const R th = A.isothermal ? R(0) : (en[k] - R(2) * drho[k] - rho * (ux * ux + uy * uy)) * R(0.5) * inv;
+        uyv[k] = uy;
+        R s = R(0), h = R(0);
+        equilibrium_dev<VS, N, R>(A.tab, drho[k], rho, ux, uy, th, [&](auto ac, R deq) {
+            constexpr int a = decltype(ac)::value;
+            const R f = ft[a][k];
+            s = fma(A.tab.xixy[a], f - deq, s);
+            if constexpr (KIND == kStep) {
+                h = fma(f * f, A.tab.winv[a], h);
+                ft[a][k] = fma(omega, deq - f, f);
+            }
+        });
+        sig[k] = s * A.sigma_fac;
+        hh[k] = h;
+        if constexpr (KIND == kMoments) {
+            if (g.own) {
+                const long long c = (long long)y * A.nx + g.x + k;
+                if (A.o_rho) A.o_rho[c] = (double)A.rho0 + (double)drho[k];
+                if (A.o_ux) A.o_ux[c] = (double)ux;
+                if (A.o_uy) A.o_uy[c] = (double)uy;
+                if (A.o_T) A.o_T[c] = 1.0 + (double)th;
+                if (A.o_sxy) A.o_sxy[c] = (double)sig[k];
+                if (A.o_pop) {
+                    const long long pl = (long long)A.ny * A.nx;
+#pragma unroll
+                    for (int a = 0; a < Q; ++a)
+                        A.o_pop[a * pl + c] = (double)A.tab.w[a] * (double)A.rho0 + (double)ft[a][k];
+                }
+            }
+        }
+    }
+    if constexpr (KIND == kStep) {
+        if (g.own) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                R v[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) v[k] = ft[a][k];
+                store_cells<S, R, V>(A, dst + (long long)a * A.plane + A.origin, g.x, y, v,
+                                     store_scale<S, R>(A.tab, a));
+            }
+        }
+        if (diag) {
+            R v6[6] = {0, 0, 0, 0, 0, 0};
+            if (g.own) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    v6[0] += drho[k];
+                    v6[1] += jx[k];
+                    v6[2] += jy[k];
+                    v6[3] = fma(uyv[k], A.sinx[g.x + k], v6[3]);
+                    v6[4] = fma(sig[k], A.cosx[g.x + k], v6[4]);
+                    v6[5] += hh[k];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const R sm = warp_sum(v6[i]);
+                if (lane == 0) acc[i] += (double)sm;
+            }
+        }
+    }
+}
+
+// End of a step launch: per-block FP64 partials, last-block fixed-order sum into
+// the diagnostics ring, level advance.  All threads of the block call it.
+template <class R, int NWARPS_DIAG>
+__device__ __forceinline__ void finish_step(const Args<R>& A, const double (&acc)[6], long long lvl, bool diag,
+                                            int warp, int lane) {
+    __shared__ double red[NWARPS_DIAG][6];
+    __shared__ bool is_last;
+    __shared__ double tot[6];
+    if (diag && lane == 0 && warp < NWARPS_DIAG) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) red[warp][i] = acc[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (diag) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                double s = 0.0;
+                for (int w = 0; w < NWARPS_DIAG; ++w) s += red[w][i];
+                A.partials[(long long)blockIdx.x * kDiagSlots + i] = s;
+            }
+        }
+        __threadfence();
+        const unsigned int t = atomicAdd(A.ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (diag) {
+        if (warp < 6) {
+            double s = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(A.partials + (long long)b * kDiagSlots + warp);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) tot[warp] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double ncell = (double)A.nx * (double)A.ny;
+            const double norm = 2.0 / ncell;
+            lb_diag r;
+            r.t = (double)lvl * A.dt;
+            r.mass = ncell * (double)A.rho0 + tot[0];
+            r.mom_x = tot[1];
+            r.mom_y = tot[2];
+            r.amp = tot[3] * norm;
+            r.shear = tot[4] * norm;
+            r.hnorm = tot[5];
+            const bool bad = !(isfinite(r.mass) && isfinite(r.amp) && isfinite(r.hnorm));
+            r.flags = bad ? 1.0 : 0.0;
+            if (bad) atomicOr(A.status, 1);
+            const long long rec = lvl / A.diag_every;
+            A.ring[rec % A.ring_cap] = r;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *A.level = lvl + 1;
+        *A.ticket = 0u;
+        __threadfence();
+    }
+}
+
+// ------------------------------------------------------------ register kernel
 // KIND = kStep:    f* (next level) into dst, diagnostics when due.
 // KIND = kMoments: per-cell rho, u, T, sigma_xy (and optionally f~) of the level; no store.
-template <class VS, int N, class S, class R, int V, int KIND>
-__global__ void __launch_bounds__(kThreads) lb_fused_kernel(const __grid_constant__ Args<R> A) {
+template <class VS, int N, class S, class R, int KIND>
+__global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
+    lb_fused_kernel(const __grid_constant__ Args<R> A) {
     constexpr int Q = VS::Q;
+    constexpr int V = Cfg<VS, S>::V;
+    constexpr int ROWS = Cfg<VS, S>::ROWS;
     constexpr int TW = 32 * V;
-    using St = Streamer<VS, S, R, V>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const S* __restrict__ src = static_cast<const S*>(A.src);
     S* __restrict__ dst = static_cast<S*>(A.dst);
@@ -299,204 +515,298 @@ __global__ void __launch_bounds__(kThreads) lb_fused_kernel(const __grid_constan
         diag = (A.diag_every > 0) && (lvl % A.diag_every == 0);
     }
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    const R omega = A.omega;
 
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int ty = tile / A.ntiles_x;
         const int tx = tile - ty * A.ntiles_x;
-        const int y = ty * kRows + warp;
+        const int y = ty * ROWS + warp;
         if (y >= A.ny) continue;  // warp-uniform
-        const int x0 = tx * TW;
-        const int x = x0 + lane * V;
-        const bool active = x < A.nx;
-        const int xl = active ? x : 0;
+        const int tile_start = tx * TW;
+        const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
+        const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
 
         R ft[Q][V];
-        if (A.raw) {
-            static_for<0, Q>([&](auto ac) {
-                constexpr int a = decltype(ac)::value;
-                const R sc = load_scale<S, R>(A.tab, a);
-                const S* p = src + (long long)a * A.plane + (long long)y * A.pitch + xl;
+        static_for<0, Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            const R sc = load_scale<S, R>(A.tab, a);
+            const S* pl = src + (long long)a * A.plane + A.origin;
+            if (A.raw) {
+                const S* p = pl + (long long)y * A.pitch + g.xl;
                 if constexpr (V == 2) {
                     ld2<S, R>(p, sc, ft[a][0], ft[a][1]);
                 } else {
                     ft[a][0] = ld1<S, R>(p, sc);
                 }
-            });
-        } else if constexpr (VS::kOnLattice) {
-            const bool interior = (x0 - VS::kHalo >= 0) && (x0 + TW + VS::kHalo <= A.nx);
-            static_for<0, Q>([&](auto ac) {
-                constexpr int a = decltype(ac)::value;
-                St::template shift<a>(A, src, y, interior, xl, ft[a]);
-            });
-        } else {
-            const int ym = (y == 0) ? A.ny - 1 : y - 1;
-            const int yp = (y + 1 == A.ny) ? 0 : y + 1;
-            static_for<0, Q>([&](auto ac) {
-                constexpr int a = decltype(ac)::value;
-                St::template laxw<a>(A, src, y, ym, yp, lane, xl, ft[a]);
-            });
-        }
-
-        // moments of f~ (deviation form)
-        R drho[V], jx[V], jy[V], en[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) drho[k] = jx[k] = jy[k] = en[k] = R(0);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const R ax = A.tab.a[VS::ix(a)], ay = A.tab.a[VS::iy(a)], a2 = A.tab.xi2[a];
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                drho[k] += ft[a][k];
-                jx[k] = fma(ax, ft[a][k], jx[k]);
-                jy[k] = fma(ay, ft[a][k], jy[k]);
-                en[k] = fma(a2, ft[a][k], en[k]);
-            }
-        }
-
-        R sig[V], hh[V], uyv[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const R rho = A.rho0 + drho[k];
-            const R inv = R(1) / rho;
-            const R ux = jx[k] * inv, uy = jy[k] * inv;
-            const R th = A.isothermal ? R(0) : (en[k] - R(2) * drho[k] - rho * (ux * ux + uy * uy)) * R(0.5) * inv;
-            uyv[k] = uy;
-            R s = R(0), h = R(0);
-            equilibrium_dev<VS, N, R>(A.tab, drho[k], rho, ux, uy, th, [&](auto ac, R deq) {
-                constexpr int a = decltype(ac)::value;
-                const R f = ft[a][k];
-                s = fma(A.tab.xixy[a], f - deq, s);
-                if constexpr (KIND == kStep) {
-                    h = fma(f * f, A.tab.winv[a], h);
-                    ft[a][k] = fma(omega, deq - f, f);
+            } else if constexpr (VS::kOnLattice) {
+                // exact shift: f~_a(x, y) = f*_a(x - ex, y - ey)
+                constexpr int ex = VS::ex(a), ey = VS::ey(a);
+                const S* p = pl + (long long)(y - ey) * A.pitch + g.xl - ex;
+                if constexpr (V == 2 && (ex % 2 == 0)) {
+                    ld2<S, R>(p, sc, ft[a][0], ft[a][1]);
                 } else {
-                    (void)h;
-                }
-            });
-            sig[k] = s * A.sigma_fac;
-            hh[k] = h;
-            if constexpr (KIND == kMoments) {
-                if (active && (x + k) < A.nx) {
-                    const long long c = (long long)y * A.nx + x + k;
-                    if (A.o_rho) A.o_rho[c] = (double)A.rho0 + (double)drho[k];
-                    if (A.o_ux) A.o_ux[c] = (double)ux;
-                    if (A.o_uy) A.o_uy[c] = (double)uy;
-                    if (A.o_T) A.o_T[c] = 1.0 + (double)th;
-                    if (A.o_sxy) A.o_sxy[c] = (double)sig[k];
-                    if (A.o_pop) {
-                        const long long pl = (long long)A.ny * A.nx;
 #pragma unroll
-                        for (int a = 0; a < Q; ++a)
-                            A.o_pop[a * pl + c] = (double)A.tab.w[a] * (double)A.rho0 + (double)ft[a][k];
-                    }
+                    for (int k = 0; k < V; ++k) ft[a][k] = ld1<S, R>(p + k, sc);
+                }
+            } else {
+                // tensor-product Lax-Wendroff: y pass in registers, x pass by shuffles;
+                // the warp's two edge lanes take their outer neighbour from one extra column
+                constexpr int ix = VS::ix(a), iy = VS::iy(a);
+                const R ly0 = A.tab.lw[iy][0], ly1 = A.tab.lw[iy][1], ly2 = A.tab.lw[iy][2];
+                const R lx0 = A.tab.lw[ix][0], lx1 = A.tab.lw[ix][1], lx2 = A.tab.lw[ix][2];
+                const S* r0 = pl + (long long)y * A.pitch;
+                const S* rm = r0 - A.pitch;
+                const S* rp = r0 + A.pitch;
+                R f0[V], fm[V], fp[V];
+                if constexpr (V == 2) {
+                    ld2<S, R>(r0 + g.xl, sc, f0[0], f0[1]);
+                    ld2<S, R>(rm + g.xl, sc, fm[0], fm[1]);
+                    ld2<S, R>(rp + g.xl, sc, fp[0], fp[1]);
+                } else {
+                    f0[0] = ld1<S, R>(r0 + g.xl, sc);
+                    fm[0] = ld1<S, R>(rm + g.xl, sc);
+                    fp[0] = ld1<S, R>(rp + g.xl, sc);
+                }
+                const int xe = (lane == 31) ? min(x0 + TW, A.nx) : x0 - 1;
+                const R ge = fma(ly0, ld1<S, R>(rm + xe, sc), fma(ly1, ld1<S, R>(r0 + xe, sc), ly2 * ld1<S, R>(rp + xe, sc)));
+                R gv[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) gv[k] = fma(ly0, fm[k], fma(ly1, f0[k], ly2 * fp[k]));
+                R gl = __shfl_up_sync(0xffffffffu, gv[V - 1], 1);
+                R gr = __shfl_down_sync(0xffffffffu, gv[0], 1);
+                gl = (lane == 0) ? ge : gl;
+                gr = (lane == 31) ? ge : gr;
+                if constexpr (V == 2) {
+                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1]));
+                    ft[a][1] = fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr));
+                } else {
+                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
                 }
             }
-        }
-
-        if constexpr (KIND == kStep) {
-            if (active) {
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    S* p = dst + (long long)a * A.plane + (long long)y * A.pitch + x;
-                    const R si = store_scale<S, R>(A.tab, a);
-                    if constexpr (V == 2) {
-                        st2<S, R>(p, ft[a][0], ft[a][1], si);
-                    } else {
-                        st1<S, R>(p, ft[a][0], si);
-                    }
-                }
-            }
-            if (diag) {
-                R v6[6] = {0, 0, 0, 0, 0, 0};
-                if (active) {
-#pragma unroll
-                    for (int k = 0; k < V; ++k) {
-                        v6[0] += drho[k];
-                        v6[1] += jx[k];
-                        v6[2] += jy[k];
-                        v6[3] = fma(uyv[k], A.sinx[x + k], v6[3]);
-                        v6[4] = fma(sig[k], A.cosx[x + k], v6[4]);
-                        v6[5] += hh[k];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const R s = warp_sum(v6[i]);
-                    if (lane == 0) acc[i] += (double)s;
-                }
-            }
-        }
+        });
+        collide_store<VS, N, S, R, V, KIND>(A, ft, dst, y, g, diag, acc, lane);
     }
+    if constexpr (KIND == kStep) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
+}
 
-    if constexpr (KIND == kStep) {
-        __shared__ double red[kRows][6];
-        __shared__ bool is_last;
-        if (diag) {
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) red[warp][i] = acc[i];
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (diag) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    double s = 0.0;
-                    for (int w = 0; w < kRows; ++w) s += red[w][i];
-                    A.partials[(long long)blockIdx.x * kDiagSlots + i] = s;
-                }
-            }
-            __threadfence();
-            const unsigned int t = atomicAdd(A.ticket, 1u);
-            is_last = (t == gridDim.x - 1);
-        }
-        __syncthreads();
-        if (is_last) {
-            __threadfence();
-            if (diag) {
-                __shared__ double tot[6];
-                if (warp < 6) {
-                    double s = 0.0;
-                    for (int b = lane; b < (int)gridDim.x; b += 32)
-                        s += __ldcg(A.partials + (long long)b * kDiagSlots + warp);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) tot[warp] = s;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    const double ncell = (double)A.nx * (double)A.ny;
-                    const double norm = 2.0 / ncell;
-                    lb_diag r;
-                    r.t = (double)lvl * A.dt;
-                    r.mass = ncell * (double)A.rho0 + tot[0];
-                    r.mom_x = tot[1];
-                    r.mom_y = tot[2];
-                    r.amp = tot[3] * norm;
-                    r.shear = tot[4] * norm;
-                    r.hnorm = tot[5];
-                    const bool bad = !(isfinite(r.mass) && isfinite(r.amp) && isfinite(r.hnorm));
-                    r.flags = bad ? 1.0 : 0.0;
-                    if (bad) atomicOr(A.status, 1);
-                    const long long rec = lvl / A.diag_every;
-                    A.ring[rec % A.ring_cap] = r;
-                }
-            }
-            if (threadIdx.x == 0) {
-                *A.level = lvl + 1;
-                *A.ticket = 0u;
-                __threadfence();
-            }
+// ------------------------------------------------------------ TMA-staged step kernel
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity: gives up after ~2^31 cycles
+// (about a second), flags LB_ERR_TIMEOUT in the status word and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && clock64() - t0 > (1LL << 31)) {
+            atomicOr(status, 2);
+            return false;
         }
     }
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+#ifndef LB_TMA_MAXREG
+#define LB_TMA_MAXREG 224
+#endif
+template <class VS, int N, class S>
+__global__ void __maxnreg__(LB_TMA_MAXREG)
+    lb_tma_step_kernel(const __grid_constant__ Args<float> A) {
+    using R = float;
+    using C = TmaCfg<VS, S>;
+    constexpr int Q = VS::Q, V = C::V, ROWS = C::ROWS, TW = C::TW, AL = C::AL;
+    constexpr int NS = C::NS, NG = C::NG, K = C::K, BW = C::BW, BOX = C::BOX, SLOT = C::SLOT;
+    constexpr int STAGE_ELEMS = C::STAGE_BYTES / (int)sizeof(S);
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations must be 128-byte aligned: align the base explicitly
+    unsigned char* const smem_raw =
+        smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    S* const stages = reinterpret_cast<S*>(smem_raw);
+    uint64_t* const full = reinterpret_cast<uint64_t*>(smem_raw + NS * C::STAGE_BYTES);
+    uint64_t* const empty = full + NS;
+    __shared__ int s_abort;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ROWS);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const long long lvl = __ldcg(A.level);
+    const bool diag = (A.diag_every > 0) && (lvl % A.diag_every == 0);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    volatile int* abort_flag = &s_abort;
+
+    if (warp == ROWS) {
+        // ---------------- producer: one thread streams the boxes of every tile
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < A.ntiles && !*abort_flag; tile += gridDim.x) {
+                const int ty = tile / A.ntiles_x;
+                const int tx = tile - ty * A.ntiles_x;
+                const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tx * TW;
+                const int y0 = ty * ROWS;
+                for (int grp = 0; grp < NG; ++grp, ++it) {
+                    const int s = (int)(it % NS);
+                    if (it >= (uint32_t)NS && !mbar_wait(&empty[s], ((it / NS) + 1) & 1u, A.status)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    const int a0 = grp * K;
+                    const int na = (Q - a0) < K ? (Q - a0) : K;
+                    S* dstage = stages + (long long)s * STAGE_ELEMS;
+                    if constexpr (C::LW) {
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)(K * BOX * sizeof(S)));
+                        const int xs = ((x0 - 1 + kGhostX) / AL) * AL;
+                        tma_load_3d(dstage, &A.tmap, &full[s], xs, y0 - 1 + A.gy, a0);
+                    } else {
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)(na * BOX * sizeof(S)));
+                        for (int j = 0; j < na; ++j) {
+                            const int a = a0 + j;
+                            const int xs = ((x0 - VS::ex(a) + kGhostX) / AL) * AL;
+                            tma_load_3d(dstage + j * SLOT, &A.tmap, &full[s], xs, y0 - VS::ey(a) + A.gy, a);
+                        }
+                    }
+                }
+            }
+            // drain: no box may still be in flight when the block exits
+            if (*abort_flag) {
+                const uint32_t first = it > (uint32_t)NS ? it - NS : 0u;
+                for (uint32_t k = first; k < it; ++k) mbar_wait(&full[k % NS], (k / NS) & 1u, A.status);
+            }
+        }
+    } else {
+        // ---------------- consumers: warp w owns row y0 + w of every tile
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+            const int ty = tile / A.ntiles_x;
+            const int tx = tile - ty * A.ntiles_x;
+            const int tile_start = tx * TW;
+            const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
+            const int y = ty * ROWS + warp;
+            const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
+            R ft[Q][V];
+            bool ok = true;
+            static_for<0, NG>([&](auto gc) {
+                constexpr int grp = decltype(gc)::value;
+                const int s = (int)(it % NS);
+                if (ok) {
+                    ok = !*abort_flag && mbar_wait(&full[s], (it / NS) & 1u, A.status);
+                    if (!ok) *abort_flag = 1;
+                }
+                if (ok) {
+                    const S* st = stages + (long long)s * STAGE_ELEMS;
+                    static_for<0, K>([&](auto jc) {
+                        constexpr int j = decltype(jc)::value;
+                        constexpr int a = grp * K + j;
+                        if constexpr (a < Q) {
+                            const R sc = load_scale<S, R>(A.tab, a);
+                            const S* box = st + j * SLOT;
+                            if constexpr (C::LW) {
+                                constexpr int ix = VS::ix(a), iy = VS::iy(a);
+                                const R ly0 = A.tab.lw[iy][0], ly1 = A.tab.lw[iy][1], ly2 = A.tab.lw[iy][2];
+                                const R lx0 = A.tab.lw[ix][0], lx1 = A.tab.lw[ix][1], lx2 = A.tab.lw[ix][2];
+                                const int r = (x0 - 1 + kGhostX) & (AL - 1);
+                                const S* rm = box + warp * BW;
+                                const S* r0 = rm + BW;
+                                const S* rp = r0 + BW;
+                                const int c = r + 1 + lane * V;
+                                R f0[V], fm[V], fp[V];
+                                if constexpr (V == 2) {
+                                    sld2<S, R>(r0 + c, sc, f0[0], f0[1]);
+                                    sld2<S, R>(rm + c, sc, fm[0], fm[1]);
+                                    sld2<S, R>(rp + c, sc, fp[0], fp[1]);
+                                } else {
+                                    f0[0] = sld1<S, R>(r0 + c, sc);
+                                    fm[0] = sld1<S, R>(rm + c, sc);
+                                    fp[0] = sld1<S, R>(rp + c, sc);
+                                }
+                                const int ce = (lane == 31) ? r + 1 + TW : r;
+                                const R ge = fma(ly0, sld1<S, R>(rm + ce, sc),
+                                                 fma(ly1, sld1<S, R>(r0 + ce, sc), ly2 * sld1<S, R>(rp + ce, sc)));
+                                R gv[V];
+#pragma unroll
+                                for (int k = 0; k < V; ++k) gv[k] = fma(ly0, fm[k], fma(ly1, f0[k], ly2 * fp[k]));
+                                R gl = __shfl_up_sync(0xffffffffu, gv[V - 1], 1);
+                                R gr = __shfl_down_sync(0xffffffffu, gv[0], 1);
+                                gl = (lane == 0) ? ge : gl;
+                                gr = (lane == 31) ? ge : gr;
+                                if constexpr (V == 2) {
+                                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1]));
+                                    ft[a][1] = fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr));
+                                } else {
+                                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
+                                }
+                            } else {
+                                constexpr int ex = VS::ex(a);
+                                const int r = (x0 - ex + kGhostX) & (AL - 1);
+                                const S* p = box + warp * BW + r + lane * V;
+                                if constexpr (V == 2 && (ex % 2 == 0)) {
+                                    sld2<S, R>(p, sc, ft[a][0], ft[a][1]);
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < V; ++k) ft[a][k] = sld1<S, R>(p + k, sc);
+                                }
+                            }
+                        }
+                    });
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                }
+                ++it;
+            });
+            if (!ok) break;
+            if (y >= A.ny) continue;
+            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane);
+        }
+    }
+    __syncthreads();
+    finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
+}
+
 // ------------------------------------------------------------ init kernel
-// f~(0) = f^eq(rho, u, T) per cell (raw layout, no streaming), written to dst.
+// f~(0) = f^eq(rho, u, T) per cell (raw layout, no streaming), written to dst with its images.
 template <class VS, int N, class S, class R>
-__global__ void __launch_bounds__(kThreads) lb_init_kernel(const __grid_constant__ Args<R> A) {
+__global__ void __launch_bounds__(256) lb_init_kernel(const __grid_constant__ Args<R> A) {
     S* __restrict__ dst = static_cast<S*>(A.dst);
     const long long ncell = (long long)A.nx * A.ny;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
@@ -517,31 +827,62 @@ __global__ void __launch_bounds__(kThreads) lb_init_kernel(const __grid_constant
         const R th = A.isothermal ? R(0) : (R)(T - 1.0);
         equilibrium_dev<VS, N, R>(A.tab, drho, (R)rho, (R)ux, (R)uy, th, [&](auto ac, R deq) {
             constexpr int a = decltype(ac)::value;
-            st1<S, R>(dst + (long long)a * A.plane + (long long)y * A.pitch + x, deq, store_scale<S, R>(A.tab, a));
+            const R v[1] = {deq};
+            store_cells<S, R, 1>(A, dst + (long long)a * A.plane + A.origin, x, y, v, store_scale<S, R>(A.tab, a));
         });
     }
 }
 
 // ------------------------------------------------------------ dispatch
-// kind = -1 queries the resident blocks per SM of the step kernel into *(int*)args.
 template <class VS, int N, class S, class R>
 cudaError_t launch_typed(const Launch& L) {
-    constexpr int V = cells_per_thread(VS::Q);
-    if (L.kind == -1) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            static_cast<int*>(const_cast<void*>(L.args)), lb_fused_kernel<VS, N, S, R, V, kStep>, kThreads, 0);
+    using C = Cfg<VS, S>;
+    using T = TmaCfg<VS, S>;
+    constexpr bool kTma = std::is_same<R, float>::value && T::NS >= 2;
+    if (L.kind == kQueryShape) {
+        Shape* sh = static_cast<Shape*>(const_cast<void*>(L.args));
+        sh->V = C::V;
+        sh->rows = C::ROWS;
+        sh->threads = C::THREADS;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &sh->occupancy, lb_fused_kernel<VS, N, S, R, kStep>, C::THREADS, 0);
+        if (e != cudaSuccess) return e;
+        sh->tma = 0;
+        if constexpr (kTma) {
+            e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     T::SMEM);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->tma_occupancy, lb_tma_step_kernel<VS, N, S>,
+                                                              T::THREADS, T::SMEM);
+            if (e != cudaSuccess) return e;
+            sh->tma = sh->tma_occupancy > 0 ? 1 : 0;
+            sh->tma_V = T::V;
+            sh->tma_rows = T::ROWS;
+            sh->tma_threads = T::THREADS;
+            sh->tma_smem = T::SMEM;
+            sh->box_w = T::BW;
+            sh->box_h = T::BH;
+            sh->box_d = T::BOX_D;
+        }
+        return cudaSuccess;
     }
     const Args<R>& A = *static_cast<const Args<R>*>(L.args);
     switch (L.kind) {
         case kStep:
-            lb_fused_kernel<VS, N, S, R, V, kStep><<<L.grid, kThreads, 0, L.stream>>>(A);
+            lb_fused_kernel<VS, N, S, R, kStep><<<L.grid, C::THREADS, 0, L.stream>>>(A);
             break;
         case kMoments:
-            lb_fused_kernel<VS, N, S, R, V, kMoments><<<L.grid, kThreads, 0, L.stream>>>(A);
+            lb_fused_kernel<VS, N, S, R, kMoments><<<L.grid, C::THREADS, 0, L.stream>>>(A);
             break;
         case kInit:
-            lb_init_kernel<VS, N, S, R><<<L.grid, kThreads, 0, L.stream>>>(A);
+            lb_init_kernel<VS, N, S, R><<<L.grid, 256, 0, L.stream>>>(A);
             break;
+        case kStepTma:
+            if constexpr (kTma) {
+                lb_tma_step_kernel<VS, N, S><<<L.grid, T::THREADS, T::SMEM, L.stream>>>(A);
+                break;
+            }
+            return cudaErrorNotSupported;
         default:
             return cudaErrorInvalidValue;
     }

@@ -14,11 +14,13 @@ class Lattice:
     precision: "f32" (default), "f64", "bf16", "f16" (16-bit: GH sets only).
     stream: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
     or None for a stream the handle creates.
+    step_kernel: "auto", "plain" (coalesced loads) or "tma" (TMA-staged); same results.
     """
 
     def __init__(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, precision: str = "f32",
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
-                 diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None):
+                 diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None,
+                 step_kernel: str = "auto"):
         p = capi.lb_params_default()
         p.quadrature = capi.QUADRATURES[quadrature]
         p.n_eq, p.nx, p.ny, p.kn = n_eq, nx, ny, kn
@@ -29,6 +31,7 @@ class Lattice:
         p.diag_capacity = diag_capacity
         p.storage_scale = storage_scale
         p.stream = stream
+        p.step_kernel = {"auto": 0, "plain": 1, "tma": 2}[step_kernel]
         self.quadrature, self.n_eq, self.nx, self.ny = quadrature, n_eq, nx, ny
         self.h = capi.lb_create_ex(p)
         inf = capi.lb_get_info(self.h)
