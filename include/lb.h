@@ -159,6 +159,15 @@ lb_status lb_populations(lb_handle *h, double *f);
  * oldest first, into out; *n_out receives the count.  Synchronises. */
 lb_status lb_diagnostics(lb_handle *h, lb_diag *out, int max_records, int *n_out);
 
+/* Decay rate of the shear-wave amplitude (FP64, host): minus the least-squares
+ * slope of ln|A(n)| against t over the diagnostics records with t >= t_start,
+ * up to the first record whose |A| falls below floor_rel * |A(0)|.  Needs the
+ * records to be still in the ring (capacity).  *rate and *npoints on LB_OK;
+ * LB_ERR_ARG when fewer than 3 records qualify.  Also returns, if not NULL,
+ * the fitted sigma_xy amplitude ratio: max|S(n)| / |A(0)| over the window. */
+lb_status lb_fit_decay(lb_handle *h, double t_start, double floor_rel, double *rate, int *npoints,
+                       double *shear_ratio);
+
 /* Wait for the handle's work; reports device-side errors. */
 lb_status lb_synchronize(lb_handle *h);
 
@@ -178,6 +187,68 @@ const char *lb_last_error(const lb_handle *h);
  * (on-lattice only); pass NULL arrays to query *q and *degree only. */
 lb_status lb_quadrature_info(lb_quadrature quad, int *q, int *degree, double *xi, double *w,
                              int *e);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many small, uneven shear-wave instances advanced together by one
+ * persistent kernel launch per lb_batch_run (CUDA-graph replay).  Slots can be
+ * added and removed between runs (continuous batching); admission is by the
+ * device-memory budget of the batch arena.  Lax-Wendroff product sets only.
+ * Each instance starts from the shear wave u_y = u0 sin(x_i) (rho = T = 1) and
+ * records A(n), S(n) (as in lb_diag) for every level it processes.  The per-cell
+ * arithmetic is the single-lattice one: an instance's populations are bitwise
+ * the same alone or in any mix, and bitwise those of an lb_handle run (F32).
+ * ------------------------------------------------------------------------- */
+typedef struct lb_batch lb_batch;
+
+typedef struct {
+    lb_quadrature quadrature; /* LB_D2Q16_GH, LB_D2Q36_GH or LB_D2Q64_GH */
+    int n_eq;                 /* 2..4 (degree >= N + 2) */
+    int nx, ny;               /* nx >= 2, ny >= 1 */
+    double kn;                /* Knudsen number, the batch's kn_convention */
+    double u0;                /* shear-wave amplitude */
+    int max_steps;            /* last time level to process (levels 0..max_steps) */
+    double stop_ratio;        /* stop at the first level n > 0 with sqrt(H(n)/H(0)) <= stop_ratio (0: never) */
+} lb_instance_desc;
+
+typedef struct {
+    lb_precision precision;   /* LB_F32 (default), LB_F16 or LB_BF16 deviation storage */
+    lb_kn_convention kn_convention;
+    size_t budget_bytes;      /* device arena for populations, histories, tables (default 1 GiB) */
+    int max_slots;            /* default 4096 */
+    int threads;              /* threads per CTA (64..512, multiple of 32); 0 = 256 */
+    int smem_bytes;           /* on-chip instance budget per CTA (bytes); -1 = 96 KiB */
+    void *stream;             /* cudaStream_t; NULL = own stream */
+} lb_batch_params;
+
+typedef struct {
+    int level;                /* levels processed: records 0..level-1 exist */
+    int done;                 /* 1: finished (stop rule, max_steps or non-finite) */
+    int status;               /* bit 0: non-finite state */
+    int q;
+    double dt, omega, tau;
+    size_t bytes;             /* arena bytes held by the slot */
+} lb_instance_state;
+
+void lb_batch_params_default(lb_batch_params *p);
+lb_status lb_batch_create(const lb_batch_params *p, lb_batch **out);
+/* Admit one instance; *slot receives its id.  LB_ERR_BUDGET if the arena has no room. */
+lb_status lb_batch_add(lb_batch *b, const lb_instance_desc *d, int *slot);
+/* Release a slot (its arena memory is reusable by the next add). */
+lb_status lb_batch_remove(lb_batch *b, int slot);
+/* One launch: every live, unfinished slot advances by up to `chunk` levels
+ * (0 = until it finishes).  Asynchronous on the batch stream. */
+lb_status lb_batch_run(lb_batch *b, int chunk);
+/* Wait for the batch stream and refresh the host view of every slot. */
+lb_status lb_batch_sync(lb_batch *b);
+lb_status lb_batch_state(lb_batch *b, int slot, lb_instance_state *out);
+/* A(n), S(n) of levels 0..min(level, max)-1 into caller host arrays (either may be NULL). */
+lb_status lb_batch_history(lb_batch *b, int slot, double *amp, double *shear, int max, int *n_out);
+/* FP64 decay-rate fit of a slot's history (same rule as lb_fit_decay). */
+lb_status lb_batch_fit(lb_batch *b, int slot, double t_start, double floor_rel, double *rate, int *npoints);
+size_t lb_batch_bytes_in_use(const lb_batch *b);
+long long lb_batch_kernel_launches(const lb_batch *b);
+lb_status lb_batch_destroy(lb_batch *b);
+const char *lb_batch_last_error(const lb_batch *b);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,7 @@ on the CPU.
 """
 from __future__ import annotations
 
-__all__ = ["Lattice", "capi", "build"]
+__all__ = ["Lattice", "Batch", "capi", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -24,4 +24,6 @@ def __getattr__(name):
         return importlib.import_module(".capi", __name__)
     if name == "Lattice":
         return importlib.import_module(".lattice", __name__).Lattice
+    if name == "Batch":
+        return importlib.import_module(".batch", __name__).Batch
     raise AttributeError(name)

@@ -60,6 +60,29 @@ class lb_info_t(ctypes.Structure):
     ]
 
 
+class lb_instance_desc(ctypes.Structure):
+    _fields_ = [
+        ("quadrature", ctypes.c_int), ("n_eq", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("kn", ctypes.c_double), ("u0", ctypes.c_double), ("max_steps", ctypes.c_int),
+        ("stop_ratio", ctypes.c_double),
+    ]
+
+
+class lb_batch_params(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int), ("kn_convention", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+        ("max_slots", ctypes.c_int), ("threads", ctypes.c_int), ("smem_bytes", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lb_instance_state(ctypes.Structure):
+    _fields_ = [
+        ("level", ctypes.c_int), ("done", ctypes.c_int), ("status", ctypes.c_int), ("q", ctypes.c_int),
+        ("dt", ctypes.c_double), ("omega", ctypes.c_double), ("tau", ctypes.c_double), ("bytes", ctypes.c_size_t),
+    ]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"liblb.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -85,6 +108,21 @@ def _load() -> ctypes.CDLL:
         "lb_destroy": (ctypes.c_int, [H]),
         "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_last_error": (ctypes.c_char_p, [H]),
+        "lb_fit_decay": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int), dp]),
+        "lb_batch_params_default": (None, [ctypes.POINTER(lb_batch_params)]),
+        "lb_batch_create": (ctypes.c_int, [ctypes.POINTER(lb_batch_params), ctypes.POINTER(H)]),
+        "lb_batch_add": (ctypes.c_int, [H, ctypes.POINTER(lb_instance_desc), ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_remove": (ctypes.c_int, [H, ctypes.c_int]),
+        "lb_batch_run": (ctypes.c_int, [H, ctypes.c_int]),
+        "lb_batch_sync": (ctypes.c_int, [H]),
+        "lb_batch_state": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(lb_instance_state)]),
+        "lb_batch_history": (ctypes.c_int, [H, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_fit": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                        ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_bytes_in_use": (ctypes.c_size_t, [H]),
+        "lb_batch_kernel_launches": (ctypes.c_longlong, [H]),
+        "lb_batch_destroy": (ctypes.c_int, [H]),
+        "lb_batch_last_error": (ctypes.c_char_p, [H]),
         "lb_quadrature_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), dp, dp,
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -103,6 +141,9 @@ EXPORTS = [
     "lb_params_default", "lb_create", "lb_create_ex", "lb_init_shear_wave", "lb_init_fields", "lb_step",
     "lb_moments", "lb_moments_device", "lb_populations", "lb_diagnostics", "lb_synchronize", "lb_get_info",
     "lb_kernel_launches", "lb_destroy", "lb_status_string", "lb_last_error", "lb_quadrature_info",
+    "lb_fit_decay", "lb_batch_params_default", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
+    "lb_batch_run", "lb_batch_sync", "lb_batch_state", "lb_batch_history", "lb_batch_fit",
+    "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
 ]
 
 
@@ -195,6 +236,14 @@ def lb_kernel_launches(h) -> int:
     return int(lib.lb_kernel_launches(h))
 
 
+def lb_fit_decay(h, t_start: float, floor_rel: float = 1e-4):
+    rate = ctypes.c_double()
+    n = ctypes.c_int()
+    sr = ctypes.c_double()
+    check(lib.lb_fit_decay(h, t_start, floor_rel, ctypes.byref(rate), ctypes.byref(n), ctypes.byref(sr)), h)
+    return rate.value, n.value, sr.value
+
+
 def lb_destroy(h):
     return check(lib.lb_destroy(h))
 
@@ -212,3 +261,75 @@ def lb_quadrature_info(quadrature):
         check(lib.lb_quadrature_info(q, None, None, None, None, e_arr))
         e = np.array(e_arr, dtype=np.int64).reshape(-1, 2)
     return {"q": nq.value, "degree": deg.value, "xi": xi.reshape(-1, 2), "w": w, "e": e}
+
+
+# ---- batches -----------------------------------------------------------------------------
+
+def check_batch(status: int, b=None):
+    if status != LB_OK:
+        msg = lib.lb_batch_last_error(b)
+        raise LBError(status, msg.decode() if msg else "")
+    return status
+
+
+def lb_batch_params_default() -> lb_batch_params:
+    p = lb_batch_params()
+    lib.lb_batch_params_default(ctypes.byref(p))
+    return p
+
+
+def lb_batch_create(p: lb_batch_params):
+    b = ctypes.c_void_p()
+    check_batch(lib.lb_batch_create(ctypes.byref(p), ctypes.byref(b)))
+    return b
+
+
+def lb_batch_add(b, d: lb_instance_desc) -> int:
+    slot = ctypes.c_int()
+    check_batch(lib.lb_batch_add(b, ctypes.byref(d), ctypes.byref(slot)), b)
+    return slot.value
+
+
+def lb_batch_remove(b, slot: int):
+    return check_batch(lib.lb_batch_remove(b, slot), b)
+
+
+def lb_batch_run(b, chunk: int = 0):
+    return check_batch(lib.lb_batch_run(b, chunk), b)
+
+
+def lb_batch_sync(b):
+    return check_batch(lib.lb_batch_sync(b), b)
+
+
+def lb_batch_state(b, slot: int) -> lb_instance_state:
+    st = lb_instance_state()
+    check_batch(lib.lb_batch_state(b, slot, ctypes.byref(st)), b)
+    return st
+
+
+def lb_batch_history(b, slot: int, max_records: int):
+    amp = np.empty(max(1, max_records))
+    shear = np.empty(max(1, max_records))
+    n = ctypes.c_int()
+    check_batch(lib.lb_batch_history(b, slot, _dptr(amp), _dptr(shear), max_records, ctypes.byref(n)), b)
+    return amp[: n.value].copy(), shear[: n.value].copy()
+
+
+def lb_batch_fit(b, slot: int, t_start: float, floor_rel: float = 1e-4):
+    rate = ctypes.c_double()
+    n = ctypes.c_int()
+    check_batch(lib.lb_batch_fit(b, slot, t_start, floor_rel, ctypes.byref(rate), ctypes.byref(n)), b)
+    return rate.value, n.value
+
+
+def lb_batch_bytes_in_use(b) -> int:
+    return int(lib.lb_batch_bytes_in_use(b))
+
+
+def lb_batch_kernel_launches(b) -> int:
+    return int(lib.lb_batch_kernel_launches(b))
+
+
+def lb_batch_destroy(b):
+    return check_batch(lib.lb_batch_destroy(b))

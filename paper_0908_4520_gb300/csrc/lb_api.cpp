@@ -61,17 +61,6 @@ size_t storage_bytes(lb_precision p) {
     }
 }
 
-double hermite_he(int k, double x) {
-    double h0 = 1.0, h1 = x;
-    if (k == 0) return 1.0;
-    for (int j = 1; j < k; ++j) {
-        const double h2 = x * h1 - j * h0;
-        h0 = h1;
-        h1 = h2;
-    }
-    return h1;
-}
-
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -199,27 +188,7 @@ struct lb_handle {
         A.ring = ring;
         A.ring_cap = p.diag_capacity;
         A.status = status;
-        lbk::Tab<R>& t = A.tab;
-        for (int i = 0; i < vs.na; ++i) {
-            t.a[i] = (R)vs.axis[i];
-            double fact = 1.0;
-            for (int k = 0; k <= lbk::kMaxN; ++k) {
-                if (k > 1) fact *= k;
-                t.hn[i][k] = (R)(hermite_he(k, vs.axis[i]) / fact);
-            }
-            const double C = vs.on_lattice ? 0.0 : vs.axis[i] * dt / dx;
-            t.lw[i][0] = (R)(0.5 * C * (1.0 + C));
-            t.lw[i][1] = (R)(1.0 - C * C);
-            t.lw[i][2] = (R)(-0.5 * C * (1.0 - C));
-        }
-        for (int a = 0; a < vs.q; ++a) {
-            t.w[a] = (R)vs.w[a];
-            t.winv[a] = (R)(1.0 / vs.w[a]);
-            t.xixy[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a + 1]);
-            t.xi2[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a] + vs.xi[2 * a + 1] * vs.xi[2 * a + 1]);
-            t.sc[a] = (R)(vs.w[a] * scale);
-            t.scinv[a] = (R)(1.0 / (vs.w[a] * scale));
-        }
+        lbh::build_tab<R>(vs, dt, dx, scale, A.tab);
     }
 
 };
@@ -737,6 +706,40 @@ lb_status lb_diagnostics(lb_handle* h, lb_diag* out, int max_records, int* n_out
     }
     *n_out = (int)cnt;
     return st;
+}
+
+lb_status lb_fit_decay(lb_handle* h, double t_start, double floor_rel, double* rate, int* npoints,
+                       double* shear_ratio) {
+    if (!h || !rate || !npoints) return h ? h->fail(LB_ERR_ARG, "null output") : LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_fit_decay before an init call");
+    const long long total = h->level + 1;
+    if (total > h->p.diag_capacity) return h->fail(LB_ERR_ARG, "records no longer in the ring (raise diag_capacity)");
+    std::vector<lb_diag> rec((size_t)total);
+    int n = 0;
+    lb_status st = lb_diagnostics(h, rec.data(), (int)total, &n);
+    if (st != LB_OK) return st;
+    const double a0 = std::fabs(rec[0].amp);
+    double st_ = 0, sl = 0, stt = 0, stl = 0, smax = 0;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (rec[i].t < t_start) continue;
+        const double a = std::fabs(rec[i].amp);
+        if (!(a >= floor_rel * a0) || a == 0.0) break;
+        const double l = std::log(a);
+        st_ += rec[i].t;
+        sl += l;
+        stt += rec[i].t * rec[i].t;
+        stl += rec[i].t * l;
+        smax = std::max(smax, std::fabs(rec[i].shear));
+        ++m;
+    }
+    if (m < 3) return h->fail(LB_ERR_ARG, "fewer than 3 records in the fit window");
+    const double den = m * stt - st_ * st_;
+    if (!(den > 0)) return h->fail(LB_ERR_ARG, "degenerate fit window");
+    *rate = -(m * stl - st_ * sl) / den;
+    *npoints = m;
+    if (shear_ratio) *shear_ratio = a0 > 0 ? smax / a0 : 0.0;
+    return LB_OK;
 }
 
 lb_status lb_get_info(const lb_handle* h, lb_info_t* o) {

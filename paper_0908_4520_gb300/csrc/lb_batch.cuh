@@ -1,0 +1,196 @@
+// Persistent multi-instance kernel: many small, uneven lattices in one launch.
+//
+// Each CTA takes instances from a work queue (an atomic counter over a list
+// ordered by decreasing remaining cost, i.e. longest-processing-time first) and
+// advances one instance at a time by up to `chunk` time levels, with a block
+// barrier between levels: an instance never spans CTAs, so no CTA ever waits
+// on another.  An instance whose two population buffers fit the CTA's shared
+// memory is copied in once per chunk and stepped entirely on chip; larger ones
+// step through global memory (L2-resident at these sizes).  The per-cell
+// arithmetic is collide_cell(), the same function the single-lattice kernels
+// call, so a lattice's populations are bitwise the same whichever path runs it
+// and whatever else shares the launch.  Lax-Wendroff streaming only: the
+// batch serves the Gauss-Hermite product sets.
+#pragma once
+
+#include "lb_batch.h"
+#include "lb_kernels.cuh"
+
+namespace lbk {
+
+template <class S>
+__device__ __forceinline__ float batch_load(const S* p, float sc) {
+    if constexpr (Is16<S>::value) {
+        return (std::is_same<S, __half>::value ? __half2float(*reinterpret_cast<const __half*>(p))
+                                               : __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p))) *
+               sc;
+    } else {
+        (void)sc;
+        return *p;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void batch_store(S* p, float v, float scinv) {
+    st1<S, float>(p, v, scinv);
+}
+
+// Advance instance `id` by up to B.chunk levels with the CTA's threads.
+template <class VS, int N, class S>
+__device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
+    constexpr int Q = VS::Q;
+    BatchInst& in = B.inst[id];
+    const Tab<float>& t = B.tab[in.set];
+    const int nx = in.nx, ny = in.ny;
+    const int ncell = nx * ny;
+    const long long pop = (long long)Q * ncell;
+    const float omega = in.omega, sigma_fac = in.sigma_fac;
+    const float* sinx = B.trig + in.trig_off;
+    const float* cosx = sinx + nx;
+    float2* hist = B.hist + in.hist_off;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+    __shared__ float red[32][3];
+    __shared__ int s_done;
+
+    int level = in.level;
+    int cur = in.cur;
+    const int stop = min(in.max_level, level + B.chunk - 1);
+    // per-velocity storage scales
+    const bool onchip = 2 * pop * (long long)sizeof(S) <= (long long)B.smem_cap;
+    S* const arena = static_cast<S*>(B.arena);
+    S* gbuf[2] = {arena + in.off[0], arena + in.off[1]};
+    S* buf[2] = {gbuf[0], gbuf[1]};
+    if (onchip) {
+        buf[0] = smem;
+        buf[1] = smem + pop;
+        if (level > 0)
+            for (long long k = tid; k < pop; k += nthr) buf[cur][k] = gbuf[cur][k];
+    }
+    if (tid == 0) s_done = in.done;
+    __syncthreads();
+
+    const float scale = in.scale;
+    for (; level <= stop && !s_done; ++level) {
+        const S* src = buf[cur];
+        S* dst = buf[level == 0 ? 0 : 1 - cur];
+        float pa = 0.f, ps = 0.f, ph = 0.f;
+        bool bad = false;
+        for (int c = tid; c < ncell; c += nthr) {
+            const int y = c / nx, x = c - y * nx;
+            float ft[Q];
+            if (level == 0) {
+                // f~(0) = f^eq(rho = 1, u_y = u0 sin x, T = 1), rounded through the storage type
+                const double sx = sinpi(2.0 * (double)x / (double)nx);
+                const float uy = (float)(in.u0 * sx);
+                equilibrium_dev<VS, N, float>(t, 0.f, 1.f, 0.f, uy, 0.f, [&](auto ac, float deq) {
+                    constexpr int a = decltype(ac)::value;
+                    if constexpr (Is16<S>::value) {
+                        S tmp;
+                        st1<S, float>(&tmp, deq, 1.0f / (t.w[a] * scale));
+                        ft[a] = batch_load<S>(&tmp, t.w[a] * scale);
+                    } else {
+                        ft[a] = deq;
+                    }
+                });
+            } else {
+                const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
+                const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int a = decltype(ac)::value;
+                    constexpr int ix = VS::ix(a), iy = VS::iy(a);
+                    const float sc = Is16<S>::value ? t.w[a] * scale : 1.f;
+                    const S* pl = src + (long long)a * ncell;
+                    const float ly0 = t.lw[iy][0], ly1 = t.lw[iy][1], ly2 = t.lw[iy][2];
+                    const float lx0 = t.lw[ix][0], lx1 = t.lw[ix][1], lx2 = t.lw[ix][2];
+                    auto col = [&](int xc) {
+                        return fma(ly0, batch_load<S>(pl + ym * nx + xc, sc),
+                                   fma(ly1, batch_load<S>(pl + y * nx + xc, sc), ly2 * batch_load<S>(pl + yp * nx + xc, sc)));
+                    };
+                    const float gl = col(xm), g0 = col(x), gr = col(xp);
+                    ft[a] = fma(lx0, gl, fma(lx1, g0, lx2 * gr));
+                });
+            }
+            const CellOut<float> co = collide_cell<VS, N, float, float, true>(
+                t, 1.f, omega, sigma_fac, in.isothermal, true,
+                [&](auto ac) -> float& { return ft[decltype(ac)::value]; });
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                batch_store<S>(dst + (long long)a * ncell + c, ft[a], Is16<S>::value ? 1.0f / (t.w[a] * scale) : 1.f);
+            pa = fma(co.uy, sinx[x], pa);
+            ps = fma(co.sig, cosx[x], ps);
+            ph += co.h;
+            bad |= !isfinite(co.h);
+        }
+        pa = warp_sum(pa);
+        ps = warp_sum(ps);
+        ph = warp_sum(ph);
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            red[warp][0] = pa;
+            red[warp][1] = ps;
+            red[warp][2] = bad ? __int_as_float(0x7fc00000) : ph;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double A = 0, Sx = 0, H = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                A += red[w][0];
+                Sx += red[w][1];
+                H += red[w][2];
+            }
+            const double norm = 2.0 / (double)ncell;
+            hist[level] = make_float2((float)(A * norm), (float)(Sx * norm));
+            if (level == 0) in.h0 = (float)H;
+            int d = 0;
+            if (!isfinite(H)) {
+                in.status |= 1;
+                d = 1;
+            }
+            if (level > 0 && (double)H <= (double)in.stop_ratio2 * (double)in.h0) d = 1;
+            if (level == in.max_level) d = 1;
+            s_done = d;
+        }
+        cur = (level == 0) ? 0 : 1 - cur;
+        __syncthreads();
+    }
+    if (onchip && level > in.level)
+        for (long long k = tid; k < pop; k += nthr) gbuf[cur][k] = buf[cur][k];
+    if (tid == 0) {
+        in.level = level;
+        in.cur = cur;
+        in.done = s_done;
+    }
+    __syncthreads();
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    S* smem = reinterpret_cast<S*>(bsm);
+    __shared__ int s_i;
+    for (;;) {
+        if (threadIdx.x == 0) s_i = atomicAdd(B.next, 1);
+        __syncthreads();
+        const int i = s_i;
+        __syncthreads();
+        if (i >= *B.n_order) break;
+        const int id = B.order[i];
+        const BatchInst& in = B.inst[id];
+        if (in.done) continue;
+        switch (in.set * 3 + (in.n_eq - 2)) {
+            case 0: batch_run<lbvs::GH4, 2, S>(B, id, smem); break;
+            case 1: batch_run<lbvs::GH4, 3, S>(B, id, smem); break;
+            case 2: batch_run<lbvs::GH4, 4, S>(B, id, smem); break;
+            case 3: batch_run<lbvs::GH6, 2, S>(B, id, smem); break;
+            case 4: batch_run<lbvs::GH6, 3, S>(B, id, smem); break;
+            case 5: batch_run<lbvs::GH6, 4, S>(B, id, smem); break;
+            case 6: batch_run<lbvs::GH8, 2, S>(B, id, smem); break;
+            case 7: batch_run<lbvs::GH8, 3, S>(B, id, smem); break;
+            case 8: batch_run<lbvs::GH8, 4, S>(B, id, smem); break;
+            default: break;
+        }
+    }
+}
+
+}  // namespace lbk

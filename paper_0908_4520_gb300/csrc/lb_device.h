@@ -23,7 +23,10 @@ constexpr int kGhostX = 8;     // ghost columns kept on each side of a populatio
 template <class R>
 struct Tab {
     R a[kMaxNA];              // axis node values (xi components)
+    R a2[kMaxNA];             // a_i^2
+    R wm[kMaxNA];             // 1-D marginal weights W_i (product-weight sets: w_a = W[ix] W[iy])
     R hn[kMaxNA][kMaxN + 1];  // He_k(a_i) / k!
+    R whn[kMaxNA][kMaxN + 1]; // W_i He_k(a_i) / k!
     R lw[kMaxNA][3];          // Lax-Wendroff weights of f*(x-1), f*(x), f*(x+1)
     R w[kMaxQ];               // quadrature weights
     R winv[kMaxQ];            // 1 / w

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "lb.h"
+#include "lb_device.h"
 
 namespace lbh {
 
@@ -25,5 +26,41 @@ struct VelocitySetInfo {
 void gauss_hermite(int n, std::vector<double>& x, std::vector<double>& w);
 int exact_degree(const VelocitySetInfo& vs, double tol);
 bool build_velocity_set(lb_quadrature quad, VelocitySetInfo* out, std::string* err);
+
+double hermite_he(int k, double x);
+
+// Kernel tables of a velocity set (FP64 on the host, rounded once to R):
+// axis nodes, He_k(a_i)/k!, Lax-Wendroff weights for Courant numbers a_i dt/dx,
+// weights and their inverses, xi_x xi_y, |xi|^2, 16-bit storage scales w S.
+template <class R>
+void build_tab(const VelocitySetInfo& vs, double dt, double dx, double scale, lbk::Tab<R>& t) {
+    t = lbk::Tab<R>{};
+    // 1-D marginal weights: W_i = sum of w_a over the velocities with ix = i
+    std::vector<double> wm(vs.na, 0.0);
+    for (int a = 0; a < vs.q; ++a) wm[vs.ix[a]] += vs.w[a];
+    for (int i = 0; i < vs.na; ++i) {
+        t.a[i] = (R)vs.axis[i];
+        t.a2[i] = (R)(vs.axis[i] * vs.axis[i]);
+        t.wm[i] = (R)wm[i];
+        double fact = 1.0;
+        for (int k = 0; k <= lbk::kMaxN; ++k) {
+            if (k > 1) fact *= k;
+            t.hn[i][k] = (R)(hermite_he(k, vs.axis[i]) / fact);
+            t.whn[i][k] = (R)(wm[i] * hermite_he(k, vs.axis[i]) / fact);
+        }
+        const double C = vs.on_lattice ? 0.0 : vs.axis[i] * dt / dx;
+        t.lw[i][0] = (R)(0.5 * C * (1.0 + C));
+        t.lw[i][1] = (R)(1.0 - C * C);
+        t.lw[i][2] = (R)(-0.5 * C * (1.0 - C));
+    }
+    for (int a = 0; a < vs.q; ++a) {
+        t.w[a] = (R)vs.w[a];
+        t.winv[a] = (R)(1.0 / vs.w[a]);
+        t.xixy[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a + 1]);
+        t.xi2[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a] + vs.xi[2 * a + 1] * vs.xi[2 * a + 1]);
+        t.sc[a] = (R)(vs.w[a] * scale);
+        t.scinv[a] = (R)(1.0 / (vs.w[a] * scale));
+    }
+}
 
 }  // namespace lbh

@@ -178,6 +178,111 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// ------------------------------------------------------------ packed lanes
+// Two cells of a thread travel as one packed pair (f2) through the paired FP32
+// instructions of sm_100-class GPUs (add/sub/mul/fma .f32x2).  Each half of a
+// pair rounds exactly as the scalar instruction would, so a pair gives the
+// results of two scalar evaluations bit for bit.
+struct __align__(8) f2 {
+    float x, y;
+};
+
+__device__ __forceinline__ unsigned long long f2_bits(f2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ f2 f2_from(unsigned long long r) {
+    f2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+    return f2_from(d);
+}
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(d);
+}
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(d);
+}
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_from(d);
+}
+__device__ __forceinline__ f2 vrcp(f2 a) { return f2{1.0f / a.x, 1.0f / a.y}; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vrcp(float a) { return 1.0f / a; }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vrcp(double a) { return 1.0 / a; }
+
+template <class T>
+struct LaneScalar {
+    using type = T;
+};
+template <>
+struct LaneScalar<f2> {
+    using type = float;
+};
+
+template <class T>
+__device__ __forceinline__ T vsplat(typename LaneScalar<T>::type c) {
+    if constexpr (std::is_same<T, f2>::value) {
+        return f2{c, c};
+    } else {
+        return c;
+    }
+}
+
+// lane K of a packed value, and packing of V lane values
+template <int K>
+__device__ __forceinline__ float lane_get(const f2& v) {
+    if constexpr (K == 0) {
+        return v.x;
+    } else {
+        return v.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ float lane_get(const float& v) {
+    return v;
+}
+template <int K>
+__device__ __forceinline__ double lane_get(const double& v) {
+    return v;
+}
+template <class T, class R>
+__device__ __forceinline__ T pack_lanes(R v0, R v1) {
+    if constexpr (std::is_same<T, f2>::value) {
+        return f2{v0, v1};
+    } else {
+        (void)v1;
+        return v0;
+    }
+}
+
+template <class R, int V>
+struct Pack {
+    using T = R;
+};
+template <>
+struct Pack<float, 2> {
+    using T = f2;
+};
+
 // ------------------------------------------------------------ configuration
 // Register kernel: cells per thread, rows per block, min resident blocks.
 // TMA kernel: consumer rows, velocities per stage, shared-memory budget.
@@ -215,7 +320,10 @@ struct Cfg {
 template <class VS, class S>
 struct TmaCfg {
     static constexpr int V = (sizeof(S) == 8) ? 1 : 2;
-    static constexpr int ROWS = LB_TMA_ROWS;            // consumer warps
+    // consumer warps: with the producer warp, 8 warps leave 255 registers a thread
+    // (two warps per SM sub-partition) for the 2 x 64 populations of D2Q64; 9 warps
+    // cap a thread at 168 registers, enough for q <= 37
+    static constexpr int ROWS = VS::Q > 40 ? 7 : LB_TMA_ROWS;
     static constexpr int TW = 32 * V;
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
     static constexpr bool LW = !VS::kOnLattice;
@@ -231,6 +339,7 @@ struct TmaCfg {
     static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
     static constexpr int NS = NS_FIT < 2 * NG ? NS_FIT : 2 * NG;
     static constexpr int THREADS = 32 * (ROWS + 1);     // + one producer warp
+    static constexpr int MAXREG = (ROWS + 1) <= 8 ? 255 : 168;
     static constexpr int SMEM = NS * STAGE_BYTES + 2 * NS * 8 + 128;  // + alignment slack
     static constexpr int BOX_D = LW ? K : 1;            // velocities per TMA box
 };
@@ -309,8 +418,37 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-// Write the lane's V values of plane `pl` (pointer to cell (0,0)) at (x, y) and at
-// every periodic image inside the ghost rim.
+// Write the lane's V values of plane `pl` (pointer to cell (0,0)) at every
+// periodic image of (x, y) inside the ghost rim (not at (x, y) itself).
+template <class S, class R, int V>
+__device__ __forceinline__ void store_images(const Args<R>& A, S* pl, int x, int y, const R (&v)[V], R si) {
+    int ylo = y;
+    while (ylo - A.ny >= -A.gy) ylo -= A.ny;
+    int xlo = x;
+    while (xlo - A.nx >= -kGhostX) xlo -= A.nx;
+    for (int yi = ylo; yi < A.ny + A.gy; yi += A.ny) {
+        for (int xi = xlo; xi + V <= A.nx + kGhostX; xi += A.nx) {
+            if (xi == x && yi == y) continue;
+            S* q = pl + (long long)yi * A.pitch + xi;
+            if constexpr (V == 2) {
+                st2<S, R>(q, v[0], v[1], si);
+            } else {
+                st1<S, R>(q, v[0], si);
+            }
+        }
+    }
+}
+
+// Out-of-line image writer (boundary lanes only), so the unrolled callers stay small.
+template <class S, class R, int V>
+__device__ __noinline__ void store_images_call(const Args<R>& A, S* pl, int x, int y, R v0, R v1, R si) {
+    R v[V];
+    v[0] = v0;
+    if constexpr (V == 2) v[V - 1] = v1;
+    store_images<S, R, V>(A, pl, x, y, v, si);
+}
+
+// Write the lane's values at (x, y) and at every periodic image.
 template <class S, class R, int V>
 __device__ __forceinline__ void store_cells(const Args<R>& A, S* pl, int x, int y, const R (&v)[V], R si) {
     S* p = pl + (long long)y * A.pitch + x;
@@ -319,108 +457,218 @@ __device__ __forceinline__ void store_cells(const Args<R>& A, S* pl, int x, int 
     } else {
         st1<S, R>(p, v[0], si);
     }
-    if (x < kGhostX || x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) {
-        int ylo = y;
-        while (ylo - A.ny >= -A.gy) ylo -= A.ny;
-        int xlo = x;
-        while (xlo - A.nx >= -kGhostX) xlo -= A.nx;
-        for (int yi = ylo; yi < A.ny + A.gy; yi += A.ny) {
-            for (int xi = xlo; xi + V <= A.nx + kGhostX; xi += A.nx) {
-                if (xi == x && yi == y) continue;
-                S* q = pl + (long long)yi * A.pitch + xi;
-                if constexpr (V == 2) {
-                    st2<S, R>(q, v[0], v[1], si);
-                } else {
-                    st1<S, R>(q, v[0], si);
-                }
-            }
-        }
-    }
+    if (x < kGhostX || x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) store_images<S, R, V>(A, pl, x, y, v, si);
 }
 
 // ------------------------------------------------------------ collision (shared)
-// Moments, equilibrium, relaxation and the store (or the moment outputs) of the
-// cells (g.x .. g.x+V-1, y) whose streamed populations are in ft.  Diagnostics
-// are reduced over the warp in FP32 and added to acc (lane 0) in FP64.
-template <class VS, int N, class S, class R, int V, int KIND>
-__device__ __forceinline__ void collide_store(const Args<R>& A, R (&ft)[VS::Q][V], S* __restrict__ dst, int y,
-                                              const Lane& g, bool diag, double (&acc)[6], int lane) {
-    constexpr int Q = VS::Q;
-    const R omega = A.omega;
-    R drho[V], jx[V], jy[V], en[V];
+// Result of colliding one cell (or a packed pair of cells).
+template <class T>
+struct CellOut {
+    T drho, jx, jy;   // deviation moments: rho - rho0, rho u
+    T ux, uy, th;     // velocity, T - 1
+    T sig;            // sigma_xy = (1 - omega/2) sum xi_x xi_y (f~ - f^eq)   (diag)
+    T h;              // sum (f~ - w rho0)^2 / w                               (diag)
+};
+
+// The one definition of the per-cell arithmetic; every kernel calls it.  The
+// streamed deviations are f(integral_constant<a>) (references, relaxed in place
+// when COLLIDE).  T is a scalar or a packed pair of cells.
+//  * moments from per-axis-node sums: C[i] = sum_{ix = i} d, Ry[j] = sum_{iy = j} d;
+//    rho - rho0 = sum C, rho u_x = sum a_i C[i], rho u_y = sum a_j Ry[j],
+//    sum |xi|^2 d = sum a_i^2 (C[i] + Ry[i])  (Sec. 2.2; kinetic T with D = 2)
+//  * diagnostics (diag): Pi_xy = sum xi_x xi_y d and H = sum d^2 / w of the
+//    streamed state; sigma_xy = (1 - omega/2) (Pi_xy - rho u_x u_y), since the
+//    truncated equilibrium carries exactly the xy moment rho u_x u_y of the
+//    Maxwellian when the quadrature degree is >= N + 2
+//  * equilibrium (Sec. 2.1), per axis: f^eq_a - w rho0 = w_a (drho + rho S'_a),
+//    S'_a = sum'_{kx+ky<=N} c_kx(u_x) c_ky(u_y) hn[ix][kx] hn[iy][ky]; for product
+//    weights w_a = W_ix W_iy the weights fold into the per-axis factors, so
+//    omega (f^eq_a - w_a rho0) = sum_{ky<=N} PX[ix][ky] QY[iy][ky]
+//  * relaxation (Eq. 2order): f* = (1 - omega) f~ + omega f^eq, one FMA a velocity
+template <class VS, int N, class R, class T, bool COLLIDE, class F>
+__device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R omega, R sigma_fac, int isothermal,
+                                                   bool diag, F&& f) {
+    constexpr int NA = VS::NA;
+    const T zero = vsplat<T>(R(0));
+    T C[NA], Ry[NA];
 #pragma unroll
-    for (int k = 0; k < V; ++k) drho[k] = jx[k] = jy[k] = en[k] = R(0);
+    for (int i = 0; i < NA; ++i) C[i] = Ry[i] = zero;
+    static_for<0, VS::Q>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        const T v = f(ac);
+        C[VS::ix(a)] = vadd(C[VS::ix(a)], v);
+        Ry[VS::iy(a)] = vadd(Ry[VS::iy(a)], v);
+    });
+    T drho = C[0], jx = vmul(vsplat<T>(t.a[0]), C[0]), jy = vmul(vsplat<T>(t.a[0]), Ry[0]);
+    T en = vmul(vsplat<T>(t.a2[0]), vadd(C[0], Ry[0]));
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const R ax = A.tab.a[VS::ix(a)], ay = A.tab.a[VS::iy(a)], a2 = A.tab.xi2[a];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            drho[k] += ft[a][k];
-            jx[k] = fma(ax, ft[a][k], jx[k]);
-            jy[k] = fma(ay, ft[a][k], jy[k]);
-            en[k] = fma(a2, ft[a][k], en[k]);
-        }
+    for (int i = 1; i < NA; ++i) {
+        drho = vadd(drho, C[i]);
+        jx = vfma(vsplat<T>(t.a[i]), C[i], jx);
+        jy = vfma(vsplat<T>(t.a[i]), Ry[i], jy);
+        en = vfma(vsplat<T>(t.a2[i]), vadd(C[i], Ry[i]), en);
     }
-    R sig[V], hh[V], uyv[V];
+    CellOut<T> o;
+    T pxy = zero, h = zero;
+    if (diag) {
+        T P[NA];
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const R rho = A.rho0 + drho[k];
-        const R inv = R(1) / rho;
-        const R ux = jx[k] * inv, uy = jy[k] * inv;
-        const R th = A.isothermal ? R(0) : (en[k] - R(2) * drho[k] - rho * (ux * ux + uy * uy)) * R(0.5) * inv;
-        uyv[k] = uy;
-        R s = R(0), h = R(0);
-        equilibrium_dev<VS, N, R>(A.tab, drho[k], rho, ux, uy, th, [&](auto ac, R deq) {
+        for (int i = 0; i < NA; ++i) P[i] = zero;
+        static_for<0, VS::Q>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
-            const R f = ft[a][k];
-            s = fma(A.tab.xixy[a], f - deq, s);
-            if constexpr (KIND == kStep) {
-                h = fma(f * f, A.tab.winv[a], h);
-                ft[a][k] = fma(omega, deq - f, f);
+            const T v = f(ac);
+            P[VS::ix(a)] = vfma(vsplat<T>(t.a[VS::iy(a)]), v, P[VS::ix(a)]);
+            h = vfma(vmul(v, vsplat<T>(t.winv[a])), v, h);
+        });
+#pragma unroll
+        for (int i = 0; i < NA; ++i) pxy = vfma(vsplat<T>(t.a[i]), P[i], pxy);
+    }
+    const T rho = vadd(vsplat<T>(rho0), drho);
+    const T inv = vrcp(rho);
+    const T ux = vmul(jx, inv), uy = vmul(jy, inv);
+    const T u2 = vfma(ux, ux, vmul(uy, uy));
+    T th = zero;
+    if (!isothermal) th = vmul(vmul(vsub(vsub(en, vadd(drho, drho)), vmul(rho, u2)), vsplat<T>(R(0.5))), inv);
+    o.drho = drho;
+    o.jx = jx;
+    o.jy = jy;
+    o.ux = ux;
+    o.uy = uy;
+    o.th = th;
+    o.sig = vmul(vsplat<T>(sigma_fac), vsub(pxy, vmul(rho, vmul(ux, uy))));
+    o.h = h;
+    if constexpr (COLLIDE) {
+        // Hermite coefficients of the Maxwellian, c_{k+1} = u c_k + k (T - 1) c_{k-1}
+        T cx[N + 1], cy[N + 1];
+        cx[0] = cy[0] = vsplat<T>(R(1));
+        cx[1] = ux;
+        cy[1] = uy;
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+            const T kth = vmul(vsplat<T>(R(k)), th);
+            cx[k + 1] = vfma(ux, cx[k], vmul(kth, cx[k - 1]));
+            cy[k + 1] = vfma(uy, cy[k], vmul(kth, cy[k - 1]));
+        }
+        T QY[NA][N + 1];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            QY[j][0] = vsplat<T>(t.wm[j]);
+#pragma unroll
+            for (int ky = 1; ky <= N; ++ky)
+                QY[j][ky] = vmul(vsplat<T>(VS::kProductWeights ? t.whn[j][ky] : t.hn[j][ky]), cy[ky]);
+        }
+        const T om1 = vsplat<T>(R(1) - omega);
+        static_for<0, NA>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            // px[0] = sum_{kx>=1} cx hn (the kx = ky = 0 term is rho itself); px[ky>=1] = sum_{kx<=N-ky} cx hn
+            T px[N + 1];
+#pragma unroll
+            for (int ky = 0; ky <= N; ++ky) {
+                T sacc = ky == 0 ? zero : vsplat<T>(R(1));
+#pragma unroll
+                for (int kx = 1; kx <= N - ky; ++kx) sacc = vfma(cx[kx], vsplat<T>(t.hn[I][kx]), sacc);
+                px[ky] = sacc;
+            }
+            if constexpr (VS::kProductWeights) {
+                const T ow = vsplat<T>(omega * t.wm[I]);
+                T PX[N + 1];
+                PX[0] = vmul(ow, vfma(rho, px[0], drho));
+                const T owr = vmul(ow, rho);
+#pragma unroll
+                for (int ky = 1; ky <= N; ++ky) PX[ky] = vmul(owr, px[ky]);
+                static_for<0, VS::Q>([&](auto ac) {
+                    constexpr int a = decltype(ac)::value;
+                    if constexpr (VS::ix(a) == I) {
+                        constexpr int iy = VS::iy(a);
+                        T od = vmul(PX[0], QY[iy][0]);
+#pragma unroll
+                        for (int ky = 1; ky <= N; ++ky) od = vfma(PX[ky], QY[iy][ky], od);
+                        T& fa = f(ac);
+                        fa = vfma(fa, om1, od);
+                    }
+                });
+            } else {
+                static_for<0, VS::Q>([&](auto ac) {
+                    constexpr int a = decltype(ac)::value;
+                    if constexpr (VS::ix(a) == I) {
+                        constexpr int iy = VS::iy(a);
+                        T sacc = px[0];
+#pragma unroll
+                        for (int ky = 1; ky <= N; ++ky) sacc = vfma(px[ky], QY[iy][ky], sacc);
+                        const T od = vmul(vsplat<T>(omega * t.w[a]), vfma(rho, sacc, drho));
+                        T& fa = f(ac);
+                        fa = vfma(fa, om1, od);
+                    }
+                });
             }
         });
-        sig[k] = s * A.sigma_fac;
-        hh[k] = h;
-        if constexpr (KIND == kMoments) {
-            if (g.own) {
+    }
+    return o;
+}
+
+// Collision and store (or the moment outputs) of the V cells (g.x .., y) whose
+// streamed populations are in ft.  Diagnostics are reduced over the warp in
+// FP32 and added to acc (lane 0) in FP64.
+template <class VS, int N, class S, class R, int V, int KIND, class T>
+__device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], S* __restrict__ dst, int y,
+                                              const Lane& g, bool diag, double (&acc)[6], int lane) {
+    constexpr int Q = VS::Q;
+    const CellOut<T> co = collide_cell<VS, N, R, T, KIND == kStep>(
+        A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments,
+        [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
+    if constexpr (KIND == kMoments) {
+        if (g.own) {
+            static_for<0, V>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
                 const long long c = (long long)y * A.nx + g.x + k;
-                if (A.o_rho) A.o_rho[c] = (double)A.rho0 + (double)drho[k];
-                if (A.o_ux) A.o_ux[c] = (double)ux;
-                if (A.o_uy) A.o_uy[c] = (double)uy;
-                if (A.o_T) A.o_T[c] = 1.0 + (double)th;
-                if (A.o_sxy) A.o_sxy[c] = (double)sig[k];
+                if (A.o_rho) A.o_rho[c] = (double)A.rho0 + (double)lane_get<k>(co.drho);
+                if (A.o_ux) A.o_ux[c] = (double)lane_get<k>(co.ux);
+                if (A.o_uy) A.o_uy[c] = (double)lane_get<k>(co.uy);
+                if (A.o_T) A.o_T[c] = 1.0 + (double)lane_get<k>(co.th);
+                if (A.o_sxy) A.o_sxy[c] = (double)lane_get<k>(co.sig);
                 if (A.o_pop) {
                     const long long pl = (long long)A.ny * A.nx;
 #pragma unroll
                     for (int a = 0; a < Q; ++a)
-                        A.o_pop[a * pl + c] = (double)A.tab.w[a] * (double)A.rho0 + (double)ft[a][k];
+                        A.o_pop[a * pl + c] = (double)A.tab.w[a] * (double)A.rho0 + (double)lane_get<k>(ft[a]);
                 }
-            }
+            });
         }
     }
     if constexpr (KIND == kStep) {
         if (g.own) {
+            S* base = dst + A.origin + (long long)y * A.pitch + g.x;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                R v[V];
-#pragma unroll
-                for (int k = 0; k < V; ++k) v[k] = ft[a][k];
-                store_cells<S, R, V>(A, dst + (long long)a * A.plane + A.origin, g.x, y, v,
-                                     store_scale<S, R>(A.tab, a));
+                S* p = base + (long long)a * A.plane;
+                const R si = store_scale<S, R>(A.tab, a);
+                if constexpr (V == 2) {
+                    st2<S, R>(p, lane_get<0>(ft[a]), lane_get<1>(ft[a]), si);
+                } else {
+                    st1<S, R>(p, lane_get<0>(ft[a]), si);
+                }
+            }
+            // periodic images in the ghost rim (boundary cells only)
+            if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) {
+                static_for<0, Q>([&](auto ac) {
+                    constexpr int a = decltype(ac)::value;
+                    store_images_call<S, R, V>(A, dst + (long long)a * A.plane + A.origin, g.x, y,
+                                               lane_get<0>(ft[a]), lane_get<V - 1>(ft[a]), store_scale<S, R>(A.tab, a));
+                });
             }
         }
         if (diag) {
             R v6[6] = {0, 0, 0, 0, 0, 0};
             if (g.own) {
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    v6[0] += drho[k];
-                    v6[1] += jx[k];
-                    v6[2] += jy[k];
-                    v6[3] = fma(uyv[k], A.sinx[g.x + k], v6[3]);
-                    v6[4] = fma(sig[k], A.cosx[g.x + k], v6[4]);
-                    v6[5] += hh[k];
-                }
+                static_for<0, V>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    v6[0] += lane_get<k>(co.drho);
+                    v6[1] += lane_get<k>(co.jx);
+                    v6[2] += lane_get<k>(co.jy);
+                    v6[3] = fma(lane_get<k>(co.uy), A.sinx[g.x + k], v6[3]);
+                    v6[4] = fma(lane_get<k>(co.sig), A.cosx[g.x + k], v6[4]);
+                    v6[5] += lane_get<k>(co.h);
+                });
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -525,7 +773,8 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
         const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
         const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
 
-        R ft[Q][V];
+        using T = typename Pack<R, V>::T;
+        T ft[Q];
         static_for<0, Q>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
             const R sc = load_scale<S, R>(A.tab, a);
@@ -533,19 +782,24 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
             if (A.raw) {
                 const S* p = pl + (long long)y * A.pitch + g.xl;
                 if constexpr (V == 2) {
-                    ld2<S, R>(p, sc, ft[a][0], ft[a][1]);
+                    R v0, v1;
+                    ld2<S, R>(p, sc, v0, v1);
+                    ft[a] = pack_lanes<T, R>(v0, v1);
                 } else {
-                    ft[a][0] = ld1<S, R>(p, sc);
+                    ft[a] = ld1<S, R>(p, sc);
                 }
             } else if constexpr (VS::kOnLattice) {
                 // exact shift: f~_a(x, y) = f*_a(x - ex, y - ey)
                 constexpr int ex = VS::ex(a), ey = VS::ey(a);
                 const S* p = pl + (long long)(y - ey) * A.pitch + g.xl - ex;
                 if constexpr (V == 2 && (ex % 2 == 0)) {
-                    ld2<S, R>(p, sc, ft[a][0], ft[a][1]);
+                    R v0, v1;
+                    ld2<S, R>(p, sc, v0, v1);
+                    ft[a] = pack_lanes<T, R>(v0, v1);
+                } else if constexpr (V == 2) {
+                    ft[a] = pack_lanes<T, R>(ld1<S, R>(p, sc), ld1<S, R>(p + 1, sc));
                 } else {
-#pragma unroll
-                    for (int k = 0; k < V; ++k) ft[a][k] = ld1<S, R>(p + k, sc);
+                    ft[a] = ld1<S, R>(p, sc);
                 }
             } else {
                 // tensor-product Lax-Wendroff: y pass in registers, x pass by shuffles;
@@ -576,10 +830,10 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
                 gl = (lane == 0) ? ge : gl;
                 gr = (lane == 31) ? ge : gr;
                 if constexpr (V == 2) {
-                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1]));
-                    ft[a][1] = fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr));
+                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1])),
+                                             fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr)));
                 } else {
-                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
+                    ft[a] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
                 }
             }
         });
@@ -640,11 +894,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-#ifndef LB_TMA_MAXREG
-#define LB_TMA_MAXREG 224
-#endif
 template <class VS, int N, class S>
-__global__ void __maxnreg__(LB_TMA_MAXREG)
+__global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
     lb_tma_step_kernel(const __grid_constant__ Args<float> A) {
     using R = float;
     using C = TmaCfg<VS, S>;
@@ -724,7 +975,8 @@ __global__ void __maxnreg__(LB_TMA_MAXREG)
             const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
             const int y = ty * ROWS + warp;
             const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
-            R ft[Q][V];
+            using T = typename Pack<R, V>::T;
+        T ft[Q];
             bool ok = true;
             static_for<0, NG>([&](auto gc) {
                 constexpr int grp = decltype(gc)::value;
@@ -771,20 +1023,23 @@ __global__ void __maxnreg__(LB_TMA_MAXREG)
                                 gl = (lane == 0) ? ge : gl;
                                 gr = (lane == 31) ? ge : gr;
                                 if constexpr (V == 2) {
-                                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1]));
-                                    ft[a][1] = fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr));
+                                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1])),
+                                                             fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr)));
                                 } else {
-                                    ft[a][0] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
+                                    ft[a] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
                                 }
                             } else {
                                 constexpr int ex = VS::ex(a);
                                 const int r = (x0 - ex + kGhostX) & (AL - 1);
                                 const S* p = box + warp * BW + r + lane * V;
                                 if constexpr (V == 2 && (ex % 2 == 0)) {
-                                    sld2<S, R>(p, sc, ft[a][0], ft[a][1]);
+                                    R v0, v1;
+                                    sld2<S, R>(p, sc, v0, v1);
+                                    ft[a] = pack_lanes<T, R>(v0, v1);
+                                } else if constexpr (V == 2) {
+                                    ft[a] = pack_lanes<T, R>(sld1<S, R>(p, sc), sld1<S, R>(p + 1, sc));
                                 } else {
-#pragma unroll
-                                    for (int k = 0; k < V; ++k) ft[a][k] = sld1<S, R>(p + k, sc);
+                                    ft[a] = sld1<S, R>(p, sc);
                                 }
                             }
                         }

@@ -26,9 +26,8 @@
 
 namespace lbh {
 
-namespace {
-
-double he(int k, double x) {  // probabilists' Hermite polynomial
+// probabilists' Hermite polynomial He_k(x) by its three-term recurrence
+double hermite_he(int k, double x) {
     double h0 = 1.0, h1 = x;
     if (k == 0) return 1.0;
     for (int j = 1; j < k; ++j) {
@@ -38,6 +37,10 @@ double he(int k, double x) {  // probabilists' Hermite polynomial
     }
     return h1;
 }
+
+namespace {
+
+double he(int k, double x) { return hermite_he(k, x); }
 
 // eigenvalues / vectors of a small dense symmetric matrix (cyclic Jacobi)
 void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& v) {

@@ -87,6 +87,10 @@ class Lattice:
         n = int(inf.records) if max_records is None else max_records
         return capi.lb_diagnostics(self.h, max(n, 1))
 
+    def fit_decay(self, t_start: float, floor_rel: float = 1e-4):
+        """(rate, npoints, shear/amplitude ratio) from the FP64 fit of the library."""
+        return capi.lb_fit_decay(self.h, t_start, floor_rel)
+
     @property
     def info(self) -> dict:
         inf = capi.lb_get_info(self.h)

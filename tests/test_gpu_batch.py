@@ -1,0 +1,147 @@
+"""Batches of uneven instances (persistent kernel) against single lattices and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from lbtest import f32_tol, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def batch_cls():
+    lib()
+    from paper_0908_4520_gb300 import Batch
+
+    return Batch
+
+
+MIX = [("D2Q16-GH", 2, 32, 1, 0.05), ("D2Q36-GH", 3, 128, 4, 0.3), ("D2Q64-GH", 4, 64, 1, 2.0),
+       ("D2Q16-GH", 4, 1024, 4, 0.01), ("D2Q36-GH", 2, 256, 1, 1.0), ("D2Q64-GH", 3, 512, 4, 0.1),
+       ("D2Q36-GH", 4, 32, 4, 5.0), ("D2Q16-GH", 3, 64, 1, 0.5)]
+
+
+def test_batch_matches_single_lattice():
+    Batch = batch_cls()
+    Lattice, capi = lib()
+    b = Batch()
+    for quad, N, nx, ny, kn in MIX[:5]:
+        s = b.add(quad, N, nx, ny, kn, u0=1e-3, max_steps=150, stop_ratio=0.0)
+        b.run(0).sync()
+        amp, shear = b.history(s)
+        assert len(amp) == 151 and b.state(s)["done"] == 1
+        L = Lattice(quad, N, nx, ny, kn).init_shear_wave(1e-3)
+        L.step(150)
+        rec = L.diagnostics()
+        assert np.max(np.abs(amp - rec["amp"])) < 2e-6 * np.max(np.abs(rec["amp"]))
+        assert np.max(np.abs(shear - rec["shear"])) < 2e-5 * np.max(np.abs(rec["shear"])) + 1e-12
+        L.close()
+    b.close()
+
+
+def test_alone_and_in_a_mix_are_bitwise_equal():
+    Batch = batch_cls()
+    target = ("D2Q36-GH", 3, 128, 4, 0.3)
+    alone = Batch()
+    s0 = alone.add(*target, u0=1e-3, max_steps=300, stop_ratio=1e-3)
+    alone.run(0).sync()
+    mix = Batch()
+    slots = [mix.add(*m, u0=1e-3, max_steps=300, stop_ratio=1e-3) for m in MIX]
+    s1 = slots[1]
+    mix.run(0).sync()
+    a0, sh0 = alone.history(s0)
+    a1, sh1 = mix.history(s1)
+    np.testing.assert_array_equal(a0, a1)
+    np.testing.assert_array_equal(sh0, sh1)
+    alone.close()
+    mix.close()
+
+
+def test_chunked_runs_equal_one_run():
+    Batch = batch_cls()
+    one = Batch()
+    many = Batch()
+    for m in MIX:
+        one.add(*m, u0=1e-3, max_steps=200, stop_ratio=1e-3)
+        many.add(*m, u0=1e-3, max_steps=200, stop_ratio=1e-3)
+    one.run(0).sync()
+    for _ in range(40):
+        many.run(7)
+    many.sync()
+    for s in range(len(MIX)):
+        np.testing.assert_array_equal(one.history(s)[0], many.history(s)[0])
+        assert one.state(s)["level"] == many.state(s)["level"]
+    one.close()
+    many.close()
+
+
+def test_on_chip_and_global_paths_are_bitwise_equal():
+    Batch = batch_cls()
+    on = Batch(smem_bytes=96 * 1024)
+    off = Batch(smem_bytes=0)
+    for m in MIX[:4]:
+        on.add(*m, u0=1e-3, max_steps=120, stop_ratio=0.0)
+        off.add(*m, u0=1e-3, max_steps=120, stop_ratio=0.0)
+    on.run(0).sync()
+    off.run(0).sync()
+    for s in range(4):
+        np.testing.assert_array_equal(on.history(s)[0], off.history(s)[0])
+    on.close()
+    off.close()
+
+
+def test_stop_rule_and_cap():
+    Batch = batch_cls()
+    b = Batch()
+    fast = b.add("D2Q36-GH", 3, 64, 1, 2.0, u0=1e-3, max_steps=20000, stop_ratio=1e-3)  # large Kn: decays fast
+    capped = b.add("D2Q16-GH", 2, 256, 1, 0.01, u0=1e-3, max_steps=500, stop_ratio=1e-3)  # small Kn: capped
+    b.run(0).sync()
+    sf, sc = b.state(fast), b.state(capped)
+    assert sf["done"] == 1 and 2 < sf["level"] < 20001
+    assert sc["done"] == 1 and sc["level"] == 501
+    b.close()
+
+
+def test_budget_admission():
+    Batch = batch_cls()
+    Lattice, capi = lib()
+    # one D2Q64 1024 x 4 FP32 instance needs 2 MiB of populations
+    b = Batch(budget_bytes=3 << 20)
+    s = b.add("D2Q64-GH", 4, 1024, 4, 0.1, max_steps=10)
+    with pytest.raises(capi.LBError) as e:
+        b.add("D2Q64-GH", 4, 1024, 4, 0.1, max_steps=10)
+    assert e.value.status == capi.LB_ERR_BUDGET
+    b.remove(s)
+    b.add("D2Q64-GH", 4, 1024, 4, 0.1, max_steps=10)
+    b.close()
+
+
+@pytest.mark.parametrize("quad,N,nx,ny,kn", [("D2Q16-GH", 2, 64, 1, 0.1), ("D2Q64-GH", 4, 48, 4, 0.7)])
+def test_batch_matches_oracle(quad, N, nx, ny, kn):
+    Batch = batch_cls()
+    b = Batch()
+    s = b.add(quad, N, nx, ny, kn, u0=1e-3, max_steps=80, stop_ratio=0.0)
+    b.run(0).sync()
+    amp, shear = b.history(s)
+    P = oracle.Problem(quad, N, nx, ny, kn)
+    f = P.init_shear(1e-3)
+    d = P.run(f, 80)
+    assert np.max(np.abs(amp - d[:, 4])) < f32_tol(80) * 1e-3
+    assert np.max(np.abs(shear - d[:, 5])) < f32_tol(80) * 1e-3
+    b.close()
+
+
+def test_f16_storage_tracks_f32():
+    Batch = batch_cls()
+    b32 = Batch("f32")
+    b16 = Batch("f16")
+    for b in (b32, b16):
+        b.add("D2Q36-GH", 3, 128, 1, 0.2, u0=1e-4, max_steps=400, stop_ratio=0.0)
+        b.run(0).sync()
+    a32, _ = b32.history(0)
+    a16, _ = b16.history(0)
+    assert np.max(np.abs(a16 - a32)) < 2e-3 * 1e-4
+    r32, _ = b32.fit(0, 5 * 0.2 * np.sqrt(2 / np.pi))
+    r16, _ = b16.fit(0, 5 * 0.2 * np.sqrt(2 / np.pi))
+    assert abs(r16 / r32 - 1) < 1e-3
+    b32.close()
+    b16.close()
