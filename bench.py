@@ -332,6 +332,149 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+def _common(args, metric, value, unit, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Batching workload: 512 uneven instances, one persistent launch, against the plain
+    per-instance method (each instance alone on its own lattice) on a seeded sample."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_0908_4520_gb300 import Batch, Lattice, autotune, inputs
+
+    inst = inputs.batch_instances(args.instances)
+    tuned = autotune.tune(inst, "f32")
+    stream = torch.cuda.Stream()
+    qmap = {"D2Q16-GH": 16, "D2Q36-GH": 36, "D2Q64-GH": 64}
+    need = sum(2 * qmap[d["quadrature"]] * d["nx"] * d["ny"] * 4 + 8 * (d["max_steps"] + 2) + 8 * d["nx"] + 1024
+               for d in inst)
+    b = Batch("f32", budget_bytes=int(need * 1.2) + (64 << 20), threads=tuned["threads"],
+              smem_bytes=tuned["smem_bytes"], stream=stream.cuda_stream)
+    slots = [b.add(d["quadrature"], d["n_eq"], d["nx"], d["ny"], d["kn"], d["u0"], d["max_steps"], 1e-3)
+             for d in inst]
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        b.run(0)
+        ev1.record(stream)
+    b.sync()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    levels = [b.state(sl)["level"] for sl in slots]
+    cells = np.array([d["nx"] * d["ny"] for d in inst], dtype=np.float64)
+    q = np.array([qmap[d["quadrature"]] for d in inst], dtype=np.float64)
+    updates = float(np.sum(cells * np.array(levels)))
+    bytes_alg = float(np.sum(cells * np.array(levels) * 2 * q * 4))
+    # plain per-instance method on a seeded sample, scaled by cost
+    rng = np.random.default_rng(9084523)
+    sample = rng.choice(len(inst), size=min(args.plain_sample, len(inst)), replace=False)
+    t_plain, cost_s = 0.0, 0.0
+    for i in sample:
+        d = inst[i]
+        L = Lattice(d["quadrature"], d["n_eq"], d["nx"], d["ny"], d["kn"], stream=stream.cuda_stream)
+        L.init_shear_wave(d["u0"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.step(levels[i] - 1)
+        L.synchronize()
+        t_plain += time.perf_counter() - t0
+        cost_s += cells[i] * levels[i]
+        L.close()
+    t_plain_total = t_plain * updates / cost_s
+    done = sum(b.state(sl)["done"] for sl in slots)
+    _common(args, "aggregate MLUPS of 512 uneven shear-wave instances (persistent batched launch)",
+            round(updates / (ms / 1e3) / 1e6, 2), "MLUPS", {
+                "dtype": "f32", "ms_total": round(ms, 3), "instances": len(inst), "finished": int(done),
+                "cell_updates": updates, "algorithmic_bytes": bytes_alg,
+                "achieved_gbs": round(bytes_alg / (ms / 1e3) / 1e9, 1),
+                "launch_shape": {"threads": tuned["threads"], "smem_bytes": tuned["smem_bytes"], "autotuned": True},
+                "gpu_launches": b.launches,
+                "plain_per_instance": {"mlups": round(updates / t_plain_total / 1e6, 2),
+                                       "sample": f"{len(sample)} seeded instances alone, same levels, time scaled "
+                                                 "by cell updates to all instances",
+                                       "est_total_s": round(t_plain_total, 3)},
+                "speedup_vs_plain": round(t_plain_total / (ms / 1e3), 2),
+                "config": {"workload": "512 instances, nx in 32..1024, ny in {1,4}, D2Q16/36/64-GH, N 2..4, "
+                                       "Kn log-uniform 0.01..10, U0 1e-3, stop sqrt(H/H0) <= 1e-3 or 20000 levels",
+                           "seed": 9084521}})
+    b.close()
+
+
+def run_precision(args):
+    """Precision workload: D2Q64-GH, N = 4, 2048^2, U0 = 1e-4, 16-bit deviation storage
+    (stochastic rounding) against the FP32 run: MLUPS and the amplitude / decay-rate errors."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_0908_4520_gb300 import Lattice, inputs
+
+    kns = inputs.precision_kn()[: args.kn_count]
+    n = args.n_precision
+    out = {}
+    stream = torch.cuda.Stream()
+    for prec in ("f32", "f16", "bf16"):
+        rates, errs, ms_list, amps = [], [], [], []
+        for kn in kns:
+            c = inputs.precision_config(kn, prec, nx=n, steps=args.precision_steps)
+            L = Lattice(c["quadrature"], c["n_eq"], n, n, kn, precision=prec, stream=stream.cuda_stream)
+            L.init_shear_wave(c["u0"])
+            L.step(args.warmup)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                L.step(c["steps"] - args.warmup)
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_list.append(ev0.elapsed_time(ev1) / (c["steps"] - args.warmup))
+            rec = L.diagnostics()
+            amps.append(rec["amp"])
+            tau = L.info["tau"]
+            t = rec["t"]
+            t0 = min(5 * tau, t[-1] / 4)
+            try:
+                rates.append(L.fit_decay(t0)[0])
+            except Exception:
+                rates.append(float("nan"))
+            bpc = L.info["bytes_per_cell_update"]
+            L.close()
+        out[prec] = {"ms_per_step": ms_list, "rates": rates, "amps": amps, "bpc": bpc}
+    peak, _ = peaks()
+    res = {}
+    for prec in ("f32", "f16", "bf16"):
+        ms = float(np.median(out[prec]["ms_per_step"]))
+        res[prec] = {"mlups": round(n * n / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
+                     "algorithmic_bytes_per_cell": out[prec]["bpc"],
+                     "roofline_frac": round(out[prec]["bpc"] * n * n / (ms / 1e3) / 1e9 / peak, 4)}
+        if prec != "f32":
+            rel = [abs(a / b - 1) for a, b in zip(out[prec]["rates"], out["f32"]["rates"])]
+            amp_err = [float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+                       for a, b in zip(out[prec]["amps"], out["f32"]["amps"])]
+            res[prec]["decay_rate_rel_err_vs_f32"] = [round(r, 6) for r in rel]
+            res[prec]["max_decay_rate_rel_err"] = round(max(rel), 6)
+            res[prec]["max_amplitude_rel_err"] = round(max(amp_err), 6)
+    _common(args, "MLUPS of 16-bit deviation storage (D2Q64-GH, N=4) and its decay-rate error vs FP32",
+            res["f16"]["mlups"], "MLUPS", {
+                "dtype": "f16 storage, f32 arithmetic", "per_precision": res,
+                "kn": [round(k, 5) for k in kns],
+                "config": {"workload": f"shear wave {n}x{n}, D2Q64-GH, N=4, U0=1e-4, {args.precision_steps} steps, "
+                                       "Kn log-uniform 0.01..10 (seed 9084520)"}})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,11 +490,21 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "precision"])
+    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--plain-sample", type=int, default=24)
+    ap.add_argument("--n-precision", type=int, default=2048)
+    ap.add_argument("--precision-steps", type=int, default=2000)
+    ap.add_argument("--kn-count", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_gpu(args)
 

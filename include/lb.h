@@ -250,6 +250,57 @@ long long lb_batch_kernel_launches(const lb_batch *b);
 lb_status lb_batch_destroy(lb_batch *b);
 const char *lb_batch_last_error(const lb_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over batches.  Requests (shear-wave solves) are
+ * queued as they arrive; each lb_server_step admits queued requests while the
+ * device-memory budget allows, advances every admitted request by one chunk of
+ * levels (small requests as slots of one continuously batched persistent
+ * launch, large ones as lattices of their own on a second stream, so the two
+ * kinds overlap on the device), and retires the finished ones with their FP64
+ * decay-rate fit.  Finished requests are collected with lb_server_poll.
+ * ------------------------------------------------------------------------- */
+typedef struct lb_server lb_server;
+
+typedef struct {
+    lb_batch_params batch;     /* small requests (precision applies to both lanes) */
+    int chunk;                 /* levels per step (default 200) */
+    long long large_cells;     /* requests with nx*ny >= large_cells run as lattices (default 65536) */
+    size_t budget_bytes;       /* device bytes for large requests (default 8 GiB) */
+    int max_large;             /* concurrent large requests (default 4) */
+} lb_server_params;
+
+typedef struct {
+    long long id;
+    double arrival;            /* caller's clock, seconds */
+    lb_instance_desc desc;
+} lb_request;
+
+typedef struct {
+    long long id;
+    double arrival, admitted, finished; /* caller's clock at submit, at admission, at retirement */
+    int levels;                /* levels processed */
+    int status;                /* lb_status of the solve */
+    double decay_rate;         /* FP64 fit of ln|A(n)| (0 if the window had < 3 points) */
+    int fit_points;
+    double shear_amp;          /* max |S(n)| / |A(0)| over the history */
+} lb_response;
+
+void lb_server_params_default(lb_server_params *p);
+lb_status lb_server_create(const lb_server_params *p, lb_server **out);
+/* Queue a request; `now` is the caller's clock (seconds). */
+lb_status lb_server_submit(lb_server *s, const lb_request *r);
+/* One scheduling iteration at caller time `now`: admit, advance one chunk, retire.
+ * *active receives the number of admitted requests still running, *queued the
+ * number waiting. */
+lb_status lb_server_step(lb_server *s, double now, int *active, int *queued);
+/* Move up to max finished responses to out; *n_out receives the count. */
+lb_status lb_server_poll(lb_server *s, lb_response *out, int max, int *n_out);
+/* A(n), S(n) of a finished request into caller host arrays (either may be NULL);
+ * the server keeps a history until it is fetched once. */
+lb_status lb_server_history(lb_server *s, long long id, double *amp, double *shear, int max, int *n_out);
+lb_status lb_server_destroy(lb_server *s);
+const char *lb_server_last_error(const lb_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,21 @@ class lb_instance_state(ctypes.Structure):
     ]
 
 
+class lb_server_params(ctypes.Structure):
+    _fields_ = [("batch", lb_batch_params), ("chunk", ctypes.c_int), ("large_cells", ctypes.c_longlong),
+                ("budget_bytes", ctypes.c_size_t), ("max_large", ctypes.c_int)]
+
+
+class lb_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("arrival", ctypes.c_double), ("desc", lb_instance_desc)]
+
+
+class lb_response(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("arrival", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("finished", ctypes.c_double), ("levels", ctypes.c_int), ("status", ctypes.c_int),
+                ("decay_rate", ctypes.c_double), ("fit_points", ctypes.c_int), ("shear_amp", ctypes.c_double)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"liblb.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -123,6 +138,17 @@ def _load() -> ctypes.CDLL:
         "lb_batch_kernel_launches": (ctypes.c_longlong, [H]),
         "lb_batch_destroy": (ctypes.c_int, [H]),
         "lb_batch_last_error": (ctypes.c_char_p, [H]),
+        "lb_server_params_default": (None, [ctypes.POINTER(lb_server_params)]),
+        "lb_server_create": (ctypes.c_int, [ctypes.POINTER(lb_server_params), ctypes.POINTER(H)]),
+        "lb_server_submit": (ctypes.c_int, [H, ctypes.POINTER(lb_request)]),
+        "lb_server_step": (ctypes.c_int, [H, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "lb_server_poll": (ctypes.c_int, [H, ctypes.POINTER(lb_response), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "lb_server_history": (ctypes.c_int, [H, ctypes.c_longlong, dp, dp, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int)]),
+        "lb_server_destroy": (ctypes.c_int, [H]),
+        "lb_server_last_error": (ctypes.c_char_p, [H]),
         "lb_quadrature_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), dp, dp,
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -144,6 +170,8 @@ EXPORTS = [
     "lb_fit_decay", "lb_batch_params_default", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
     "lb_batch_run", "lb_batch_sync", "lb_batch_state", "lb_batch_history", "lb_batch_fit",
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
+    "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
+    "lb_server_history", "lb_server_destroy", "lb_server_last_error",
 ]
 
 
@@ -333,3 +361,53 @@ def lb_batch_kernel_launches(b) -> int:
 
 def lb_batch_destroy(b):
     return check_batch(lib.lb_batch_destroy(b))
+
+
+# ---- serving -----------------------------------------------------------------------------
+
+def check_server(status: int, s=None):
+    if status != LB_OK:
+        msg = lib.lb_server_last_error(s)
+        raise LBError(status, msg.decode() if msg else "")
+    return status
+
+
+def lb_server_params_default() -> lb_server_params:
+    p = lb_server_params()
+    lib.lb_server_params_default(ctypes.byref(p))
+    return p
+
+
+def lb_server_create(p: lb_server_params):
+    s = ctypes.c_void_p()
+    check_server(lib.lb_server_create(ctypes.byref(p), ctypes.byref(s)))
+    return s
+
+
+def lb_server_submit(s, r: lb_request):
+    return check_server(lib.lb_server_submit(s, ctypes.byref(r)), s)
+
+
+def lb_server_step(s, now: float):
+    a, q = ctypes.c_int(), ctypes.c_int()
+    check_server(lib.lb_server_step(s, now, ctypes.byref(a), ctypes.byref(q)), s)
+    return a.value, q.value
+
+
+def lb_server_poll(s, max_n: int = 4096):
+    out = (lb_response * max(1, max_n))()
+    n = ctypes.c_int()
+    check_server(lib.lb_server_poll(s, out, max_n, ctypes.byref(n)), s)
+    return [out[i] for i in range(n.value)]
+
+
+def lb_server_history(s, rid: int, max_records: int):
+    amp = np.empty(max(1, max_records))
+    shear = np.empty(max(1, max_records))
+    n = ctypes.c_int()
+    check_server(lib.lb_server_history(s, rid, _dptr(amp), _dptr(shear), max_records, ctypes.byref(n)), s)
+    return amp[: n.value].copy(), shear[: n.value].copy()
+
+
+def lb_server_destroy(s):
+    return check_server(lib.lb_server_destroy(s))

@@ -30,11 +30,6 @@ __device__ __forceinline__ float batch_load(const S* p, float sc) {
     }
 }
 
-template <class S>
-__device__ __forceinline__ void batch_store(S* p, float v, float scinv) {
-    st1<S, float>(p, v, scinv);
-}
-
 // Advance instance `id` by up to B.chunk levels with the CTA's threads.
 template <class VS, int N, class S>
 __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
@@ -114,9 +109,13 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
             const CellOut<float> co = collide_cell<VS, N, float, float, true>(
                 t, 1.f, omega, sigma_fac, in.isothermal, true,
                 [&](auto ac) -> float& { return ft[decltype(ac)::value]; });
+            uint32_t r = Is16<S>::value ? sr_seed(level, c) : 0u;
 #pragma unroll
-            for (int a = 0; a < Q; ++a)
-                batch_store<S>(dst + (long long)a * ncell + c, ft[a], Is16<S>::value ? 1.0f / (t.w[a] * scale) : 1.f);
+            for (int a = 0; a < Q; ++a) {
+                if constexpr (Is16<S>::value) r = xorshift32(r);
+                dst[(long long)a * ncell + c] =
+                    to_storage<S, float>(ft[a], Is16<S>::value ? 1.0f / (t.w[a] * scale) : 1.f, r);
+            }
             pa = fma(co.uy, sinx[x], pa);
             ps = fma(co.sig, cosx[x], ps);
             ph += co.h;

@@ -14,7 +14,14 @@ cudaError_t launch_s(const void* args, int grid, int threads, int smem, cudaStre
 
 template <class S>
 cudaError_t setup_s(int threads, int smem, int* occupancy) {
-    cudaError_t e = cudaFuncSetAttribute(lb_batch_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the attribute belongs to the kernel, not to a batch: raise it to the device limit once,
+    // so batches with different on-chip budgets can coexist
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > optin) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(lb_batch_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - 4096);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, lb_batch_kernel<S>, threads, smem);
 }

@@ -169,6 +169,68 @@ __device__ __forceinline__ R store_scale(const Tab<R>& t, int a) {
     return R(1);
 }
 
+// ---------------------------------------------------------------- stochastic rounding
+// 16-bit stores of the step kernels round stochastically (unbiased: the stored
+// value equals the FP32 value in expectation), so per-step changes smaller than
+// half a 16-bit ulp are not rounded away (the decay would stagnate).  The random
+// bits come from a counter-based generator: MurmurHash3's 32-bit finalizer of
+// (cell, level) seeds one xorshift32 stream per cell, advanced once per
+// velocity, so the result does not depend on the launch geometry.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
+__device__ __forceinline__ uint32_t sr_seed(long long level, long long cell) {
+    return fmix32((uint32_t)cell ^ fmix32((uint32_t)level * 0x9e3779b9u + 0x7f4a7c15u));
+}
+
+// storage value of a deviation (16-bit: stochastic rounding with the random bits r)
+template <class S, class R>
+__device__ __forceinline__ S to_storage(R v, R scinv, uint32_t r) {
+    if constexpr (std::is_same<S, __half>::value) {
+        return __float2half_rz(__uint_as_float(__float_as_uint(v * scinv) + (r & 0x1fffu)));
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v * scinv) + (r & 0xffffu)));
+    } else {
+        (void)scinv;
+        (void)r;
+        return v;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void store_raw(S* p, S a) {
+    *p = a;
+}
+template <class S>
+__device__ __forceinline__ void store_raw2(S* p, S a, S b) {
+    if constexpr (std::is_same<S, float>::value) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
+    } else if constexpr (std::is_same<S, double>::value) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));
+    } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        __nv_bfloat162 t;
+        t.x = a;
+        t.y = b;
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), t);
+    } else {
+        __half2 t;
+        t.x = a;
+        t.y = b;
+        __stcs(reinterpret_cast<__half2*>(p), t);
+    }
+}
+
 // compile-time loop: f(integral_constant<int, a>) for a in [A_, Q)
 template <int A_, int Q, class F>
 __device__ __forceinline__ void static_for(F&& f) {
@@ -418,10 +480,10 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-// Write the lane's V values of plane `pl` (pointer to cell (0,0)) at every
-// periodic image of (x, y) inside the ghost rim (not at (x, y) itself).
+// Write the lane's V storage values of plane `pl` (pointer to cell (0,0)) at
+// every periodic image of (x, y) inside the ghost rim (not at (x, y) itself).
 template <class S, class R, int V>
-__device__ __forceinline__ void store_images(const Args<R>& A, S* pl, int x, int y, const R (&v)[V], R si) {
+__device__ __forceinline__ void store_images(const Args<R>& A, S* pl, int x, int y, const S (&v)[V]) {
     int ylo = y;
     while (ylo - A.ny >= -A.gy) ylo -= A.ny;
     int xlo = x;
@@ -431,33 +493,43 @@ __device__ __forceinline__ void store_images(const Args<R>& A, S* pl, int x, int
             if (xi == x && yi == y) continue;
             S* q = pl + (long long)yi * A.pitch + xi;
             if constexpr (V == 2) {
-                st2<S, R>(q, v[0], v[1], si);
+                store_raw2<S>(q, v[0], v[1]);
             } else {
-                st1<S, R>(q, v[0], si);
+                store_raw<S>(q, v[0]);
             }
         }
     }
 }
 
 // Out-of-line image writer (boundary lanes only), so the unrolled callers stay small.
+// Copy the q values this thread just stored at (x.., y) to their periodic images.
 template <class S, class R, int V>
-__device__ __noinline__ void store_images_call(const Args<R>& A, S* pl, int x, int y, R v0, R v1, R si) {
-    R v[V];
-    v[0] = v0;
-    if constexpr (V == 2) v[V - 1] = v1;
-    store_images<S, R, V>(A, pl, x, y, v, si);
+__device__ __noinline__ void rim_images(const Args<R>& A, S* dst, int q, int x, int y) {
+    for (int a = 0; a < q; ++a) {
+        S* pl = dst + (long long)a * A.plane + A.origin;
+        const S* p = pl + (long long)y * A.pitch + x;
+        S v[V];
+        v[0] = p[0];
+        if constexpr (V == 2) v[V - 1] = p[1];
+        store_images<S, R, V>(A, pl, x, y, v);
+    }
 }
 
 // Write the lane's values at (x, y) and at every periodic image.
+// (round to nearest: used for the initial state)
 template <class S, class R, int V>
 __device__ __forceinline__ void store_cells(const Args<R>& A, S* pl, int x, int y, const R (&v)[V], R si) {
     S* p = pl + (long long)y * A.pitch + x;
+    S sv[V];
     if constexpr (V == 2) {
         st2<S, R>(p, v[0], v[1], si);
+        sv[0] = p[0];
+        sv[V - 1] = p[1];
     } else {
         st1<S, R>(p, v[0], si);
+        sv[0] = p[0];
     }
-    if (x < kGhostX || x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) store_images<S, R, V>(A, pl, x, y, v, si);
+    if (x < kGhostX || x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) store_images<S, R, V>(A, pl, x, y, sv);
 }
 
 // ------------------------------------------------------------ collision (shared)
@@ -611,7 +683,7 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
 // FP32 and added to acc (lane 0) in FP64.
 template <class VS, int N, class S, class R, int V, int KIND, class T>
 __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], S* __restrict__ dst, int y,
-                                              const Lane& g, bool diag, double (&acc)[6], int lane) {
+                                              const Lane& g, bool diag, double (&acc)[6], int lane, long long lvl) {
     constexpr int Q = VS::Q;
     const CellOut<T> co = collide_cell<VS, N, R, T, KIND == kStep>(
         A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments,
@@ -638,24 +710,32 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     if constexpr (KIND == kStep) {
         if (g.own) {
             S* base = dst + A.origin + (long long)y * A.pitch + g.x;
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                S* p = base + (long long)a * A.plane;
+            uint32_t r0 = 0, r1 = 0;
+            if constexpr (Is16<S>::value) {
+                r0 = sr_seed(lvl, (long long)y * A.nx + g.x);
+                r1 = sr_seed(lvl, (long long)y * A.nx + g.x + 1);
+            }
+            S* p = base;
+            static_for<0, Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
                 const R si = store_scale<S, R>(A.tab, a);
-                if constexpr (V == 2) {
-                    st2<S, R>(p, lane_get<0>(ft[a]), lane_get<1>(ft[a]), si);
-                } else {
-                    st1<S, R>(p, lane_get<0>(ft[a]), si);
+                if constexpr (Is16<S>::value) {
+                    r0 = xorshift32(r0);
+                    r1 = xorshift32(r1);
                 }
-            }
-            // periodic images in the ghost rim (boundary cells only)
-            if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy) {
-                static_for<0, Q>([&](auto ac) {
-                    constexpr int a = decltype(ac)::value;
-                    store_images_call<S, R, V>(A, dst + (long long)a * A.plane + A.origin, g.x, y,
-                                               lane_get<0>(ft[a]), lane_get<V - 1>(ft[a]), store_scale<S, R>(A.tab, a));
-                });
-            }
+                const S s0 = to_storage<S, R>(lane_get<0>(ft[a]), si, r0);
+                const S s1 = to_storage<S, R>(lane_get<V - 1>(ft[a]), si, r1);
+                if constexpr (V == 2) {
+                    store_raw2<S>(p, s0, s1);
+                } else {
+                    store_raw<S>(p, s0);
+                }
+                p += A.plane;
+            });
+            // periodic images in the ghost rim (boundary cells only): one out-of-line call
+            // that copies the values just stored, so the velocity loop above stays branch-free
+            if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy)
+                rim_images<S, R, V>(A, dst, Q, g.x, y);
         }
         if (diag) {
             R v6[6] = {0, 0, 0, 0, 0, 0};
@@ -837,7 +917,7 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
                 }
             }
         });
-        collide_store<VS, N, S, R, V, KIND>(A, ft, dst, y, g, diag, acc, lane);
+        collide_store<VS, N, S, R, V, KIND>(A, ft, dst, y, g, diag, acc, lane, lvl);
     }
     if constexpr (KIND == kStep) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
 }
@@ -858,6 +938,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// try_wait with a suspend-time hint (ns): the waiting thread sleeps in hardware
+// instead of spinning (used by the producer, whose waits are not latency-critical)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -874,15 +970,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait for the phase of the given parity: gives up after ~2^31 cycles
 // (about a second), flags LB_ERR_TIMEOUT in the status word and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, int* status) {
     const long long t0 = clock64();
     for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity)) return true;
         if ((i & 255u) == 255u && clock64() - t0 > (1LL << 31)) {
             atomicOr(status, 2);
             return false;
         }
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, status);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
@@ -1051,7 +1151,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             });
             if (!ok) break;
             if (y >= A.ny) continue;
-            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane);
+            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl);
         }
     }
     __syncthreads();
@@ -1105,7 +1205,7 @@ cudaError_t launch_typed(const Launch& L) {
         sh->tma = 0;
         if constexpr (kTma) {
             e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     T::SMEM);
+                                     T::SMEM);  // fixed per kernel: every handle of the unit asks the same
             if (e != cudaSuccess) return e;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->tma_occupancy, lb_tma_step_kernel<VS, N, S>,
                                                               T::THREADS, T::SMEM);

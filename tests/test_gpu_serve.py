@@ -1,0 +1,69 @@
+"""The request loop: every served result equals the same request solved alone."""
+import numpy as np
+import pytest
+
+from lbtest import lib
+
+pytestmark = pytest.mark.gpu
+
+REQS = [("D2Q16-GH", 2, 32, 1, 0.05), ("D2Q36-GH", 3, 128, 4, 0.3), ("D2Q64-GH", 4, 64, 1, 2.0),
+        ("D2Q36-GH", 2, 256, 1, 1.0), ("D2Q16-GH", 3, 64, 4, 0.5), ("D2Q64-GH", 3, 32, 4, 0.1),
+        ("D2Q36-GH", 3, 64, 64, 0.2)]  # the last one is "large" with large_cells = 4096
+
+
+def classes():
+    lib()
+    from paper_0908_4520_gb300 import Batch, Lattice
+    from paper_0908_4520_gb300.serve import Server
+
+    return Batch, Lattice, Server
+
+
+def test_served_results_equal_alone():
+    Batch, Lattice, Server = classes()
+    srv = Server(precision="f16", chunk=50, large_cells=4096)
+    for i, (q, N, nx, ny, kn) in enumerate(REQS):
+        srv.submit(i, 0.0, q, N, nx, ny, kn, u0=1e-4, max_steps=300, stop_ratio=1e-3)
+    done = []
+    for it in range(100):
+        srv.step(float(it))
+        done.extend(srv.poll())
+        if len(done) == len(REQS):
+            break
+    assert len(done) == len(REQS)
+    for r in done:
+        q, N, nx, ny, kn = REQS[r["id"]]
+        amp, shear = srv.history(r["id"])
+        assert r["status"] == 0 and len(amp) == r["levels"]
+        if nx * ny >= 4096:
+            L = Lattice(q, N, nx, ny, kn, precision="f16", diag_capacity=400).init_shear_wave(1e-4)
+            L.step(r["levels"] - 1)
+            rec = L.diagnostics()
+            np.testing.assert_array_equal(amp, rec["amp"])
+            L.close()
+        else:
+            b = Batch("f16")
+            s = b.add(q, N, nx, ny, kn, 1e-4, 300, 1e-3)
+            b.run(0).sync()
+            a1, s1 = b.history(s)
+            np.testing.assert_array_equal(amp, a1.astype(np.float64))
+            b.close()
+    srv.close()
+
+
+def test_admission_waits_for_memory():
+    Batch, Lattice, Server = classes()
+    # room for about two small instances at a time
+    srv = Server(precision="f32", chunk=40, budget_bytes=3 << 20, large_cells=1 << 30)
+    for i in range(8):
+        srv.submit(i, 0.0, "D2Q64-GH", 4, 1024, 1, 1.0, u0=1e-3, max_steps=120, stop_ratio=0.0)
+    done, max_active = [], 0
+    for it in range(200):
+        active, queued = srv.step(float(it))
+        max_active = max(max_active, active)
+        done.extend(srv.poll())
+        if len(done) == 8:
+            break
+    assert len(done) == 8 and max_active <= 2
+    assert all(r["levels"] == 121 for r in done)
+    srv.close()
