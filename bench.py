@@ -475,6 +475,101 @@ def run_precision(args):
                                        "Kn log-uniform 0.01..10 (seed 9084520)"}})
 
 
+def run_serve(args):
+    """Serving workload: seeded Poisson streams of shear-wave solves (10 % large 1024^2
+    D2Q36-GH, FP16 deviation storage) replayed in real time through the request loop,
+    against the same streams solved sequentially with the plain per-instance method.
+
+    The specified rate (2000/s) offers far more work than one GPU completes, so it is run
+    on a finite prefix of the stream (queue growth shows in the latency); a second stream
+    is offered at the rate that would load the sequential plain method to about 80 %."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_0908_4520_gb300 import Lattice, inputs
+    from paper_0908_4520_gb300.serve import Server, replay
+
+    def is_large(r):
+        return r["nx"] * r["ny"] >= 65536
+
+    def plain_solve(r, levels):
+        L = Lattice(r["quadrature"], r["n_eq"], r["nx"], r["ny"], r["kn"], precision="f16",
+                    diag_capacity=levels + 2)
+        L.init_shear_wave(r["u0"])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        L.step(levels - 1)
+        L.synchronize()
+        el = time.perf_counter() - t
+        L.close()
+        return el
+
+    # sequential plain method: service time per level (small lattices are launch-bound) and per
+    # cell update (large ones are bandwidth-bound), from a seeded sample solved alone at its cap
+    prefix = inputs.serving_stream(n=args.requests, rate=args.rate)
+    rng = np.random.default_rng(9084524)
+    smp = [prefix[i] for i in rng.choice(len(prefix), size=min(args.plain_sample, len(prefix)), replace=False)]
+    big = [r for r in smp if is_large(r)][:3]
+    small = [r for r in smp if not is_large(r)]
+    lv_big, lv_small = 2000, 2000
+    t_cell = sum(plain_solve(r, lv_big) for r in big) / max(1, sum(r["nx"] * r["ny"] * lv_big for r in big))
+    t_lvl = sum(plain_solve(r, lv_small) for r in small) / max(1, len(small) * lv_small)
+
+    def service(r, levels):
+        return t_cell * r["nx"] * r["ny"] * levels if is_large(r) else t_lvl * levels
+
+    def serve(reqs):
+        srv = Server(precision="f16", chunk=args.chunk, budget_bytes=32 << 30, large_budget_bytes=128 << 30,
+                     max_large=args.max_large)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        resp = replay(srv, reqs)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array([r["finished"] - r["arrival"] for r in resp])
+        levels = {r["id"]: r["levels"] for r in resp}
+        # the same requests, same arrivals and levels, solved one after another (FIFO)
+        t_free, lat_plain = 0.0, []
+        for r in reqs:
+            start = max(t_free, r["arrival"])
+            t_free = start + service(r, levels[r["id"]])
+            lat_plain.append(t_free - r["arrival"])
+        lat_plain = np.array(lat_plain)
+        return levels, {"requests": len(reqs), "completed": len(resp), "wall_s": round(wall, 3),
+                "arrival_span_s": round(max(r["arrival"] for r in reqs), 3),
+                "solves_per_s": round(len(resp) / wall, 2),
+                "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
+                              "p99": round(float(np.percentile(lat, 99)), 4)},
+                "failed": int(sum(1 for r in resp if r["status"] != 0)),
+                "sequential_plain": {"solves_per_s": round(len(reqs) / t_free, 2),
+                                     "latency_s": {"p50": round(float(np.percentile(lat_plain, 50)), 4),
+                                                   "p99": round(float(np.percentile(lat_plain, 99)), 4)}}}
+
+    lv, spec = serve(prefix)
+    # mean plain service demand of the stream (levels as served) -> rate for ~80 % utilisation
+    demand = float(np.mean([service(r, lv[r["id"]]) for r in prefix]))
+    rate80 = 0.8 / demand
+    _, util = serve(inputs.serving_stream(n=args.requests_util, rate=rate80, seed=9084523))
+    util["rate_per_s"] = round(rate80, 3)
+    _common(args, "served shear-wave solves per second with p50/p99 latency (continuous batching)",
+            spec["solves_per_s"], "solves/s", {
+                "dtype": "f16 storage, f32 arithmetic", "higher_is_better": True,
+                "as_specified_prefix": spec, "at_80pct_plain_utilisation": util,
+                "plain_service_model": {"s_per_level_small": t_lvl, "s_per_cell_update_large": t_cell,
+                                        "sample": f"{len(small)} small and {len(big)} large requests of the "
+                                                  f"stream solved alone for 2000 levels each (FP16 storage)",
+                                        "mean_demand_s": round(demand, 4)},
+                "config": {"workload": f"Poisson stream, first {args.requests} requests at {args.rate}/s (seed "
+                                       "9084522), 10% 1024^2 D2Q36-GH N=3, else nx 32..1024 x ny 1/4 "
+                                       "D2Q16/36/64-GH, N 2..4; Kn log-uniform 0.01..10, U0 1e-4, stop "
+                                       "sqrt(H/H0) <= 1e-3 or 20000 levels; FP16 deviation storage",
+                           "chunk": args.chunk, "max_large": args.max_large,
+                           "budget_gb": 160, "timing": "wall clock of the real-time replay"}})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,7 +585,12 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "precision"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "precision", "serve"])
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--requests-util", type=int, default=150)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--chunk", type=int, default=200)
+    ap.add_argument("--max-large", type=int, default=8)
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--n-precision", type=int, default=2048)
@@ -505,6 +605,8 @@ def main():
         run_batch(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

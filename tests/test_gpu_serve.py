@@ -53,10 +53,10 @@ def test_served_results_equal_alone():
 
 def test_admission_waits_for_memory():
     Batch, Lattice, Server = classes()
-    # room for about two small instances at a time
-    srv = Server(precision="f32", chunk=40, budget_bytes=3 << 20, large_cells=1 << 30)
+    # each D2Q64 1024 x 4 FP32 instance holds 2 x 1 MiB of populations: two fit in 5 MiB, three do not
+    srv = Server(precision="f32", chunk=40, budget_bytes=5 << 20, large_cells=1 << 30)
     for i in range(8):
-        srv.submit(i, 0.0, "D2Q64-GH", 4, 1024, 1, 1.0, u0=1e-3, max_steps=120, stop_ratio=0.0)
+        srv.submit(i, 0.0, "D2Q64-GH", 4, 1024, 4, 1.0, u0=1e-3, max_steps=120, stop_ratio=0.0)
     done, max_active = [], 0
     for it in range(200):
         active, queued = srv.step(float(it))
@@ -64,6 +64,6 @@ def test_admission_waits_for_memory():
         done.extend(srv.poll())
         if len(done) == 8:
             break
-    assert len(done) == 8 and max_active <= 2
+    assert len(done) == 8 and max_active == 2
     assert all(r["levels"] == 121 for r in done)
     srv.close()
