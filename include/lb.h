@@ -251,6 +251,52 @@ lb_status lb_batch_destroy(lb_batch *b);
 const char *lb_batch_last_error(const lb_batch *b);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free solve of one small shear wave.  The paper has no
+ * counterpart: this is an engineering entry point for callers that cannot
+ * allocate device memory, e.g. a process whose free device memory is already
+ * claimed by another allocator (a framework's caching allocator, a fixed
+ * per-process budget), so that cudaMalloc would fail, or a latency-critical
+ * loop that must not call cudaMalloc/cudaFree because they can synchronise the
+ * device.  It allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine): all device state of the solve (instance descriptor, work-queue
+ * counter, sin/cos table, history, both population buffers) lives in one
+ * fixed __device__ array of LB_STATIC_SCRATCH_BYTES per device.  CUDA loads
+ * device code lazily by default, so the array is reserved by the first call
+ * on a device: make that call early (at start-up, while the memory is free).
+ *
+ * The instance is the lb_batch one (same desc, same kernel, same constants):
+ * it runs from level 0 until the stop rule or max_steps, and its history is
+ * that of the same desc run in an lb_batch with default launch shape.
+ *   desc        Gauss-Hermite product set, n_eq 2..4, grid, kn, u0, max_steps, stop_ratio
+ *   precision   LB_F32, LB_F16 or LB_BF16 deviation storage (FP32 arithmetic)
+ *   history     caller host array of 2 max_records floats, or NULL if max_records = 0:
+ *               (A(n), S(n)) interleaved for levels 0..min(level, max_records)-1
+ *   state       optional; level, done, status, q, dt, omega, tau, and in `bytes`
+ *               the scratch bytes the solve used
+ *   stream      cudaStream_t to run on (NULL = the default stream); the call
+ *               returns after the solve has finished.
+ * Needs: 512 + 8 nx + 8 (max_steps + 1) + 2 q nx ny sizeof(storage) bytes
+ * (each term rounded up to 256); a larger solve returns LB_ERR_BUDGET with the
+ * sizes in lb_last_error(NULL), before any device work.  Errors: LB_ERR_ARG,
+ * LB_ERR_UNSUPPORTED, LB_ERR_CUDA, LB_ERR_UNSTABLE (non-finite state; history
+ * and state are not written); messages in lb_last_error(NULL).
+ *
+ * First call on each device: one-time set-up with that device current (the
+ * scratch's device address via cudaGetSymbolAddress, the velocity-set tables,
+ * the kernel's shared-memory attribute).  Make that first call before any
+ * stream capture begins on the device.
+ *
+ * The scratch is one array per device shared by every call on that device:
+ * calls that overlap in time (from several host threads, on any streams)
+ * race on it and return wrong results.  Serialise them.
+ * ------------------------------------------------------------------------- */
+#define LB_STATIC_SCRATCH_BYTES (8u << 20)
+
+lb_status lb_solve_static(const lb_instance_desc *desc, lb_precision precision,
+                          lb_kn_convention kn_convention, float *history, int max_records,
+                          lb_instance_state *state, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Serving: a request loop over batches.  Requests (shear-wave solves) are
  * queued as they arrive; each lb_server_step admits queued requests while the
  * device-memory budget allows, advances every admitted request by one chunk of

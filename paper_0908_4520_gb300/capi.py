@@ -18,6 +18,8 @@ LIB_PATH = os.environ.get("LB_LIB_PATH") or os.path.join(_PKG, "liblb.so")
 # lb_status
 LB_OK, LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_NOMEM, LB_ERR_CUDA = 0, -1, -2, -3, -4
 LB_ERR_UNSTABLE, LB_ERR_TIMEOUT, LB_ERR_BUDGET, LB_ERR_STATE = -5, -6, -7, -8
+# device scratch of lb_solve_static (LB_STATIC_SCRATCH_BYTES)
+LB_STATIC_SCRATCH_BYTES = 8 << 20
 
 # lb_quadrature
 QUADRATURES = {
@@ -149,6 +151,9 @@ def _load() -> ctypes.CDLL:
                                              ctypes.POINTER(ctypes.c_int)]),
         "lb_server_destroy": (ctypes.c_int, [H]),
         "lb_server_last_error": (ctypes.c_char_p, [H]),
+        "lb_solve_static": (ctypes.c_int, [ctypes.POINTER(lb_instance_desc), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                           ctypes.POINTER(lb_instance_state), ctypes.c_void_p]),
         "lb_quadrature_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), dp, dp,
                                               ctypes.POINTER(ctypes.c_int)]),
@@ -171,7 +176,7 @@ EXPORTS = [
     "lb_batch_run", "lb_batch_sync", "lb_batch_state", "lb_batch_history", "lb_batch_fit",
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
-    "lb_server_history", "lb_server_destroy", "lb_server_last_error",
+    "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static",
 ]
 
 
@@ -316,6 +321,22 @@ def lb_batch_add(b, d: lb_instance_desc) -> int:
     slot = ctypes.c_int()
     check_batch(lib.lb_batch_add(b, ctypes.byref(d), ctypes.byref(slot)), b)
     return slot.value
+
+
+def lb_solve_static(desc: lb_instance_desc, precision: int = 0, kn_convention: int = 0, max_records: int = -1,
+                    stream: int = 0):
+    """Allocation-free single solve (the library's fixed device scratch).  Returns
+    (amp, shear, state); amp/shear are the FP32 history as float64 arrays."""
+    if max_records < 0:
+        max_records = desc.max_steps + 1
+    hist = np.empty(2 * max(1, max_records), dtype=np.float32)
+    st = lb_instance_state()
+    check(lib.lb_solve_static(ctypes.byref(desc), int(precision), int(kn_convention),
+                              hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), max_records, ctypes.byref(st),
+                              stream or None))
+    n = min(st.level, max_records)
+    h = hist[: 2 * n].reshape(n, 2).astype(np.float64)
+    return h[:, 0].copy(), h[:, 1].copy(), st
 
 
 def lb_batch_remove(b, slot: int):

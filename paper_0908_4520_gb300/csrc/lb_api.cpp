@@ -339,6 +339,8 @@ lb_status init_common(lb_handle* h, double u0, double u1, const double* d_rho, c
 
 }  // namespace
 
+void lbh::set_last_error(const std::string& m) { g_create_error = m; }
+
 extern "C" {
 
 void lb_params_default(lb_params* p) {

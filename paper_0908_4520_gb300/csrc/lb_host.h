@@ -29,6 +29,9 @@ bool build_velocity_set(lb_quadrature quad, VelocitySetInfo* out, std::string* e
 
 double hermite_he(int k, double x);
 
+// Message returned by lb_last_error(NULL) on this thread.
+void set_last_error(const std::string& m);
+
 // Kernel tables of a velocity set (FP64 on the host, rounded once to R):
 // axis nodes, He_k(a_i)/k!, Lax-Wendroff weights for Courant numbers a_i dt/dx,
 // weights and their inverses, xi_x xi_y, |xi|^2, 16-bit storage scales w S.
