@@ -13,8 +13,8 @@ quadrature.py  velocity sets: Golub-Welsch Gauss-Hermite rules and products,
                the Table 1 sets from their printed surds, D2Q37 by moment
                matching.
 lb_oracle.c    plain FP64 LB stepper (moments, tensor-form Hermite
-               equilibrium of Sec. 2.1, Eq. 2order collision, exact shift or
-               Lax-Wendroff streaming, observables).
+               equilibrium and body-force term of Sec. 2.1, Eq. 2order
+               collision, exact shift or Lax-Wendroff streaming, observables).
 dvm_oracle.c   reduced linearised-BGK DVM of Sec. 3.3 (Eqs. ga, gb, unforced).
 linear.py      linear-mode matrix of the scheme and the continuous DVM
                dispersion relation (pins).
@@ -70,6 +70,7 @@ class _Params(ctypes.Structure):
         ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
         ("rho0", ctypes.c_double), ("isothermal", ctypes.c_int), ("ninner", ctypes.c_int),
         ("zin", ctypes.POINTER(ctypes.c_double)), ("win", ctypes.POINTER(ctypes.c_double)),
+        ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double), ("force_uniform", ctypes.c_int),
     ]
 
 
@@ -81,9 +82,12 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(_Params)
             lib.oracle_lb_run.argtypes = [pp, dp, ctypes.c_int, dp]
-            lib.oracle_lb_moments.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+            lib.oracle_lb_run_from.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_lb_moments.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp, dp, dp]
             lib.oracle_feq.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, dp]
+            lib.oracle_force.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, dp]
             lib.oracle_lb_init_shear.argtypes = [pp, ctypes.c_double, ctypes.c_double, dp]
             lib.oracle_dvm_run.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
@@ -106,13 +110,18 @@ def collision_time(kn: float, convention: str = "lambda") -> float:
 
 
 class Problem:
-    """One standing-shear-wave configuration for the oracle."""
+    """One standing-shear-wave configuration for the oracle.
+
+    force_amp, force_freq: body force g = (0, g_y), g_y = force_amp sin(x_i) cos(force_freq t)
+    (force_uniform: g_y = force_amp cos(force_freq t)); force_amp = 0 is the free wave."""
 
     def __init__(self, set_name: str, N: int, nx: int, ny: int, kn: float,
-                 kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False):
+                 kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
+                 force_amp: float = 0.0, force_freq: float = 0.0, force_uniform: bool = False):
         self.vs = quadrature.velocity_set(set_name)
         self.set_name, self.N, self.nx, self.ny, self.kn = set_name, N, nx, ny, kn
         self.isothermal = isothermal
+        self.force_amp, self.force_freq = force_amp, force_freq
         self.dx = 2.0 * math.pi / nx
         if self.vs.on_lattice:
             self.dt = self.dx / self.vs.c
@@ -128,7 +137,8 @@ class Problem:
         self._p = _Params(nx, ny, self.vs.Q, N, _dp(self._xi), _dp(self._w),
                           self._e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if self._e is not None else None,
                           self.dx, self.dt, self.tau, 1.0, int(isothermal), INNER_NODES,
-                          _dp(self._z), _dp(self._wz))
+                          _dp(self._z), _dp(self._wz), float(force_amp), float(force_freq),
+                          int(force_uniform))
 
     @property
     def Q(self):
@@ -139,24 +149,32 @@ class Problem:
         _load().oracle_feq(ctypes.byref(self._p), rho, ux, uy, T, _dp(out))
         return out
 
+    def force(self, rho, ux, uy, T, gy):
+        """Hermite force term g_alpha of g = (0, gy) at the Maxwellian (rho, u, T)."""
+        out = np.empty(self.Q)
+        _load().oracle_force(ctypes.byref(self._p), rho, ux, uy, T, gy, _dp(out))
+        return out
+
     def init_shear(self, u0: float, u1: float = 0.0) -> np.ndarray:
         f = np.empty((self.Q, self.ny, self.nx))
         _load().oracle_lb_init_shear(ctypes.byref(self._p), u0, u1, _dp(f))
         return f
 
-    def run(self, f: np.ndarray, nsteps: int, record: bool = True):
-        """Advance f (Q, ny, nx) in place; returns (nsteps+1, 8) records or None."""
+    def run(self, f: np.ndarray, nsteps: int, record: bool = True, n0: int = 0):
+        """Advance f (Q, ny, nx) in place from time level n0; returns (nsteps+1, 8)
+        records (levels n0..n0+nsteps) or None."""
         assert f.dtype == np.float64 and f.flags.c_contiguous and f.shape == (self.Q, self.ny, self.nx)
         diag = np.empty((nsteps + 1, 8)) if record else None
-        rc = _load().oracle_lb_run(ctypes.byref(self._p), _dp(f), nsteps, _dp(diag))
+        rc = _load().oracle_lb_run_from(ctypes.byref(self._p), _dp(f), n0, nsteps, _dp(diag))
         if rc != 0:
             raise RuntimeError("oracle_lb_run failed")
         return diag
 
-    def moments(self, f: np.ndarray) -> dict:
+    def moments(self, f: np.ndarray, n: int = 0) -> dict:
+        """Per-cell rho, u, T, sigma_xy of f~ at time level n (n sets the force phase)."""
         out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T", "sxy")}
-        _load().oracle_lb_moments(ctypes.byref(self._p), _dp(f), *(_dp(out[k]) for k in
-                                                                  ("rho", "ux", "uy", "T", "sxy")))
+        _load().oracle_lb_moments(ctypes.byref(self._p), _dp(f), n, *(_dp(out[k]) for k in
+                                                                     ("rho", "ux", "uy", "T", "sxy")))
         return out
 
 

@@ -7,21 +7,31 @@
  *
  * What it computes, step by step, in the paper's order (Sec. 2.1-2.2):
  *   state       f~_alpha(r, t)                      (the variable of Eq. 2order)
- *   moments     rho = sum f~,  rho u = sum xi f~     (Sec. 2.2, unforced)
- *               D rho T = sum |xi - u|^2 f~, D = 2   (kinetic temperature)
+ *   force       g = (0, g_y), g_y(x_i, t) = A_f sin(x_i) cos(phi t) (the standing-wave
+ *               drive of Sec. 4, Eq. force, turned so that the flow is along y and
+ *               varies along x), or a uniform g_y = A_f cos(phi t); A_f = 0: unforced
+ *   moments     rho = sum f~,  rho u = sum xi f~ + rho g dt / 2   (Sec. 2.2)
+ *               D rho T = sum |xi - u|^2 f, D = 2, of the distribution f behind
+ *               f~ (kinetic temperature; with a force T = T(f~) + dt^2 g^2 / 8)
  *   equilibrium f^eq_alpha = w_alpha sum_{n<=N} (1/n!) a_eq^(n) : chi^(n)(xi_alpha)
  *               with a_eq^(n) = int f^eq chi^(n) dxi   (Eqs. approxf, an, Sec. 2.1),
  *               the tensor contraction taken over every index tuple in {x,y}^n
  *               and each a_eq component integrated against the Maxwellian by an
  *               inner Gauss-Hermite rule (exact for these polynomial degrees).
- *   collide     f* = f~ - omega (f~ - f^eq), omega = dt / (tau + dt/2)   (Eq. 2order)
+ *   force term  g_alpha = w_alpha sum_{n=1..N} 1/(n-1)! g a_eq^(n-1) : chi^(n)(xi_alpha)
+ *               (Sec. 2.1), the contraction over every index tuple whose first
+ *               index carries g; it is the source -g . grad_xi f^eq of Eq. bgk moved
+ *               to the right-hand side (its N = 2 form is printed in Sec. 2.1)
+ *   collide     f* = f~ - omega (f~ - f^eq) + omega tau g_alpha,
+ *               omega = dt / (tau + dt/2)                                  (Eq. 2order)
  *   stream      on-lattice: f~_alpha(r + xi_alpha dt) = f*_alpha(r), an exact
  *               periodic shift by e_alpha (Sec. 2.3); off-lattice: Lax-Wendroff
  *               along x then along y (the scheme named in Sec. 3.3 and the
  *               caption of the D2Q400 figure), periodic.
  * Observables at each time level n are taken from f~(n), before collision:
  *   mass = sum rho, mom = sum rho u, A = 2/(nx ny) sum u_y sin(x_i),
- *   S = 2/(nx ny) sum sigma_xy cos(x_i), sigma_xy = (1 - omega/2) sum xi_x xi_y (f~ - f^eq),
+ *   S = 2/(nx ny) sum sigma_xy cos(x_i),
+ *   sigma_xy = (1 - omega/2) sum xi_x xi_y (f~ - f^eq + dt/2 g_alpha)  (f - f^eq of f~),
  *   H = sum (f~ - w rho0)^2 / w, x_i = i * dx.
  */
 #include <math.h>
@@ -44,6 +54,9 @@ typedef struct {
     int isothermal;      /* 1: T = 1 in the equilibrium */
     int ninner;          /* inner Gauss-Hermite rule for a_eq integrals */
     const double *zin, *win;
+    double force_amp;    /* A_f of g_y = A_f s(x_i) cos(phi t); 0: unforced */
+    double force_freq;   /* phi */
+    int force_uniform;   /* 1: s(x) = 1, 0: s(x) = sin(x_i) */
 } oracle_lb_params;
 
 /* probabilists' Hermite polynomial He_k(x) by its three-term recurrence */
@@ -98,6 +111,38 @@ void oracle_feq(const oracle_lb_params *p, double rho, double ux, double uy, dou
     for (int a = 0; a < p->Q; ++a) feq[a] *= p->w[a];
 }
 
+/* Hermite force term g_alpha for g = (0, gy) at the Maxwellian (rho, u, T):
+ * F_alpha = w_alpha sum_{n=1..N} 1/(n-1)! sum over index tuples (i1..in) with
+ * i1 = y of gy a_eq^(n-1)_(i2..in) chi^(n)_(i1..in)(xi_alpha). */
+void oracle_force(const oracle_lb_params *p, double rho, double ux, double uy, double T, double gy,
+                  double *F)
+{
+    double Teq = p->isothermal ? 1.0 : T;
+    for (int a = 0; a < p->Q; ++a) F[a] = 0.0;
+    for (int n = 1; n <= p->N; ++n) {
+        double inv = 1.0 / factorial(n - 1);
+        for (int t = 0; t < (1 << n); ++t) { /* bit b set -> index b is y; bit 0 is i1 */
+            if (!(t & 1)) continue;           /* g has no x component */
+            int ky = __builtin_popcount((unsigned)t), kx = n - ky;
+            double am1 = a_eq_component(p, rho, ux, uy, Teq, kx, ky - 1); /* a^(n-1) over i2..in */
+            for (int a = 0; a < p->Q; ++a) {
+                double chi = hermite_he(kx, p->xi[2 * a]) * hermite_he(ky, p->xi[2 * a + 1]);
+                F[a] += inv * gy * am1 * chi;
+            }
+        }
+    }
+    for (int a = 0; a < p->Q; ++a) F[a] *= p->w[a];
+}
+
+/* g_y at column x and time t */
+static double force_at(const oracle_lb_params *p, int x, double t)
+{
+    if (p->force_amp == 0.0) return 0.0;
+    const double pi = 3.14159265358979323846;
+    double s = p->force_uniform ? 1.0 : sin(2.0 * pi * (double)x / (double)p->nx);
+    return p->force_amp * s * cos(p->force_freq * t);
+}
+
 /* macroscopic moments of one cell's populations f[a * stride] */
 static void cell_moments(const oracle_lb_params *p, const double *f, size_t stride,
                          double *rho, double *ux, double *uy, double *T)
@@ -122,27 +167,37 @@ static void cell_moments(const oracle_lb_params *p, const double *f, size_t stri
 
 /* Observables of f~ and the collision into fstar (if not NULL). rec: 8 doubles. */
 static void collide_and_observe(const oracle_lb_params *p, const double *f, double *fstar,
-                                double omega, double *rec,
+                                double omega, double t, double *rec,
                                 double *orho, double *oux, double *ouy, double *oT, double *osxy)
 {
     const int nx = p->nx, ny = p->ny, Q = p->Q;
     const size_t plane = (size_t)nx * ny;
     const double pi = 3.14159265358979323846;
     double mass = 0, mx = 0, my = 0, A = 0, S = 0, H = 0;
-    double feq[ORACLE_MAXQ];
+    double feq[ORACLE_MAXQ], F[ORACLE_MAXQ];
+    const double tau = p->tau;
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
             double rho, ux, uy, T;
             cell_moments(p, f + c, plane, &rho, &ux, &uy, &T);
+            double gy = force_at(p, x, t);
+            if (gy != 0.0) {
+                /* rho u = sum xi f~ + rho g dt/2; T of f: T(f~) + dt^2 g^2 / 8 */
+                uy += 0.5 * p->dt * gy;
+                T += p->dt * p->dt * gy * gy / 8.0;
+                oracle_force(p, rho, ux, uy, T, gy, F);
+            } else {
+                for (int a = 0; a < Q; ++a) F[a] = 0.0;
+            }
             oracle_feq(p, rho, ux, uy, T, feq);
             double sxy = 0, h = 0;
             for (int a = 0; a < Q; ++a) {
                 double fa = f[(size_t)a * plane + c];
-                sxy += p->xi[2 * a] * p->xi[2 * a + 1] * (fa - feq[a]);
+                sxy += p->xi[2 * a] * p->xi[2 * a + 1] * (fa - feq[a] + 0.5 * p->dt * F[a]);
                 double d = fa - p->w[a] * p->rho0;
                 h += d * d / p->w[a];
-                if (fstar) fstar[(size_t)a * plane + c] = fa - omega * (fa - feq[a]);
+                if (fstar) fstar[(size_t)a * plane + c] = fa - omega * (fa - feq[a]) + omega * tau * F[a];
             }
             sxy *= (1.0 - 0.5 * omega);
             double xi_pos = 2.0 * pi * (double)x / (double)nx; /* x_i = i dx, dx = 2 pi / nx */
@@ -226,10 +281,10 @@ void oracle_lb_init_shear(const oracle_lb_params *p, double u0, double u1, doubl
         }
 }
 
-/* Advance f~ (Q x ny x nx, in/out) by nsteps.  diag: (nsteps + 1) x 8 records
- * (t, mass, mom_x, mom_y, A, S, H, 0) for time levels 0..nsteps, or NULL.
+/* Advance f~ (Q x ny x nx, in/out) from time level n0 by nsteps.  diag: (nsteps + 1)
+ * x 8 records (t, mass, mom_x, mom_y, A, S, H, 0) for levels n0..n0+nsteps, or NULL.
  * Returns 0, or -1 on bad arguments. */
-int oracle_lb_run(const oracle_lb_params *p, double *f, int nsteps, double *diag)
+int oracle_lb_run_from(const oracle_lb_params *p, double *f, int n0, int nsteps, double *diag)
 {
     if (!p || !f || p->Q <= 0 || p->Q > ORACLE_MAXQ || p->N < 0 || p->N > ORACLE_MAXN ||
         p->nx <= 0 || p->ny <= 0 || p->ninner > ORACLE_MAXINNER || nsteps < 0)
@@ -245,26 +300,33 @@ int oracle_lb_run(const oracle_lb_params *p, double *f, int nsteps, double *diag
     double omega = p->dt / (p->tau + 0.5 * p->dt);
     for (int s = 0; s < nsteps; ++s) {
         double *rec = diag ? diag + (size_t)s * 8 : NULL;
-        collide_and_observe(p, f, fstar, omega, rec, NULL, NULL, NULL, NULL, NULL);
-        if (rec) rec[0] = s * p->dt;
+        double t = (double)(n0 + s) * p->dt;
+        collide_and_observe(p, f, fstar, omega, t, rec, NULL, NULL, NULL, NULL, NULL);
+        if (rec) rec[0] = t;
         stream(p, fstar, f, tmp);
     }
     if (diag) {
         double *rec = diag + (size_t)nsteps * 8;
-        collide_and_observe(p, f, NULL, omega, rec, NULL, NULL, NULL, NULL, NULL);
-        rec[0] = nsteps * p->dt;
+        double t = (double)(n0 + nsteps) * p->dt;
+        collide_and_observe(p, f, NULL, omega, t, rec, NULL, NULL, NULL, NULL, NULL);
+        rec[0] = t;
     }
     free(fstar);
     free(tmp);
     return 0;
 }
 
-/* Per-cell moments of f~ (any output may be NULL). */
-int oracle_lb_moments(const oracle_lb_params *p, const double *f, double *rho, double *ux,
+int oracle_lb_run(const oracle_lb_params *p, double *f, int nsteps, double *diag)
+{
+    return oracle_lb_run_from(p, f, 0, nsteps, diag);
+}
+
+/* Per-cell moments of f~ at time level n (any output may be NULL). */
+int oracle_lb_moments(const oracle_lb_params *p, const double *f, int n, double *rho, double *ux,
                       double *uy, double *T, double *sxy)
 {
     if (!p || !f) return -1;
     double omega = p->dt / (p->tau + 0.5 * p->dt);
-    collide_and_observe(p, f, NULL, omega, NULL, rho, ux, uy, T, sxy);
+    collide_and_observe(p, f, NULL, omega, (double)n * p->dt, NULL, rho, ux, uy, T, sxy);
     return 0;
 }

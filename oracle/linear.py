@@ -17,6 +17,16 @@ Two independent descriptions of the small-amplitude shear wave u_y ~ sin(k x):
 * ``dvm_dispersion_roots``: the continuous reduced linearised BGK equation of
   Sec. 3.3, dG/dt + xi dG/dx = (u - G)/tau with u = sum_k w_k G_k, for the
   mode exp(i k x + s t): 1 = sum_k w_k / (1 + tau s + i tau k xi_k).
+
+The driven wave (body force g = (0, g_y), g_y = A_f sin x cos(phi t)) adds, to
+first order in A_f, two terms to one step: the equilibrium is taken at
+u = sum xi f~ + g dt/2 (Sec. 2.2), which adds omega w_a xi_ay g dt/2, and the
+force term of Sec. 2.1 is w_a xi_ay g, relaxed with the weight omega tau of
+Eq. 2order.  Since omega (tau + dt/2) = dt the step gains
+b_a = dt w_a xi_ay g before streaming; the measured velocity is
+u_y = sum xi_y f~ + g dt/2.  Hydrodynamic limits of the driven response
+u_y = Re(U e^{i phi t}) sin x: Navier-Stokes U = A_f / (i phi + nu), nu = tau
+(T = 1), and the R13 closed form printed in Sec. 4 (Kn there is tau).
 """
 from __future__ import annotations
 
@@ -105,3 +115,65 @@ def dvm_decay_rate(xi1d, w1d, tau, k=1.0):
     """Decay rate (-Re s) of the least-damped root of the dispersion relation."""
     s = dvm_dispersion_roots(xi1d, w1d, tau, k)
     return float(-np.max(s.real))
+
+
+def _projection(xi, w, isothermal):
+    Q = w.size
+    Pm = np.ones((Q, Q)) + np.einsum("ai,bi->ab", xi, xi)
+    if not isothermal:
+        s2 = 0.5 * np.sum(xi * xi, axis=1) - 1.0
+        Pm += np.outer(s2, s2)
+    return w[:, None] * Pm
+
+
+def lb_linear_forced_history(xi, w, omega, dx, dt, force_amp, phi, nsteps, e=None, isothermal=False):
+    """A(n), n = 0..nsteps, of the linearised scheme started at rest and driven by
+    g_y = force_amp sin(x_i) cos(phi t)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
+    theta = dx
+    if e is not None:
+        S = np.exp(-1j * np.asarray(e)[:, 0] * dx)
+    else:
+        C = xi[:, 0] * dt / dx
+        S = 1.0 - 1j * C * np.sin(theta) - C * C * (1.0 - np.cos(theta))
+    f = np.zeros(w.size, dtype=complex)
+    A = np.empty(nsteps + 1)
+    for n in range(nsteps + 1):
+        g = force_amp * np.cos(phi * n * dt) / 2j  # e^{ix} coefficient of g_y
+        A[n] = -2.0 * (np.sum(xi[:, 1] * f) + 0.5 * dt * g).imag
+        f = M @ f + S * (dt * w * xi[:, 1] * g)
+    return A
+
+
+def lb_linear_forced_response(xi, w, omega, dx, dt, phi, e=None, isothermal=False):
+    """Periodic response H of the linearised scheme: u_y -> Re(H A_f e^{i phi t}) sin x
+    for g_y = Re(A_f e^{i phi t}) sin x."""
+    xi = np.asarray(xi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
+    if e is not None:
+        S = np.exp(-1j * np.asarray(e)[:, 0] * dx)
+    else:
+        C = xi[:, 0] * dt / dx
+        S = 1.0 - 1j * C * np.sin(dx) - C * C * (1.0 - np.cos(dx))
+    z = np.exp(1j * phi * dt)
+    # unit drive sin(x) e^{i phi t}: its e^{ix} coefficient is e^{i phi t} / (2i)
+    X = np.linalg.solve(z * np.eye(w.size) - M, S * (dt * w * xi[:, 1] / 2j))
+    u_coef = np.sum(xi[:, 1] * X) + 0.5 * dt / 2j
+    return complex(2j * u_coef)
+
+
+def ns_response(nu, phi):
+    """Navier-Stokes response U / A_f = 1 / (i phi + nu) of the driven wave (k = 1)."""
+    return 1.0 / (1j * phi + nu)
+
+
+def r13_response(kn, phi):
+    """R13 response U / A_f of the driven standing shear wave, Sec. 4 (kn = tau)."""
+    i = 1j
+    num = 288 * kn**4 * i - 510 * phi * kn**3 + (520 * i - 225 * phi**2 * i) * kn**2 - 375 * phi * kn + 150 * i
+    den = (288 * phi * kn**4 + (510 * phi**2 * i - 270 * i) * kn**3 + (745 * phi - 225 * phi**3) * kn**2
+           + (375 * phi**2 * i - 150 * i) * kn + 150 * phi)
+    return complex(-num / den)
