@@ -124,9 +124,23 @@ def ncu_traffic(quad):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, diag_every_note=True):
+def workload_name(args):
+    if args.n == 4096 and args.quad == "D2Q36-GH" and args.n_eq == 3 and args.precision == "f32":
+        return WORKLOAD
+    return (f"standing shear wave {args.n}x{args.n}, {args.quad}, N={args.n_eq}, {args.precision} deviations, "
+            f"Kn={args.kn}")
+
+
+def kernel_label(args, tma):
+    st = {"f32": "float", "f64": "double", "f16": "__half", "bf16": "__nv_bfloat16"}[args.precision]
+    if tma:
+        return f"lb_tma_step_kernel<{args.quad}, {args.n_eq}, {st}>"
+    return f"lb_fused_kernel<{args.quad}, {args.n_eq}, {st}, kStep>"
+
+
+def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32"):
     stream = torch.cuda.Stream()
-    L = Lattice(quad, 3, nx, ny, kn, precision="f32", stream=stream.cuda_stream)
+    L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream)
     L.init_shear_wave(1e-3, 1e-3)
     L.step(warmup)
     L.synchronize()
@@ -164,7 +178,8 @@ def run_gpu(args):
     for quad in (args.quad, args.also):
         if not quad:
             continue
-        L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn)
+        L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn,
+                                                  args.n_eq, args.precision)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -200,6 +215,7 @@ def run_gpu(args):
         if quad == args.quad:
             main_ms = ms
             main_L = L
+            main_tma = bool(info["tma_staged"])
         else:
             L.close()
 
@@ -258,16 +274,18 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": args.precision,
         "data": "synthetic (analytic shear-wave initial condition, seeded; no dataset)",
-        "config": {"workload": WORKLOAD, "quadrature": args.quad, "n_eq": 3, "nx": nx, "ny": ny, "kn": args.kn,
-                   "u0": 1e-3, "u1": 1e-3, "storage": "f32 deviation f - w rho0",
+        "config": {"workload": workload_name(args), "quadrature": args.quad, "n_eq": args.n_eq, "nx": nx, "ny": ny,
+                   "kn": args.kn, "u0": 1e-3, "u1": 1e-3,
+                   "storage": ("f32 deviation f - w rho0" if args.precision == "f32" else
+                               f"{args.precision} deviation / power-of-two scale, stochastic rounding"),
                    "diagnostics": "every step (fused)",
                    "l2": "inputs larger than L2: two population buffers of %.2f GB each" % (bpc / 2 * ncell / 1e9),
                    "parallelism": f"independent instance per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": "lb_fused_kernel<GH6,3,float,float,2,kStep>",
+                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": kernel_label(args, main_tma),
                      "algorithmic_bytes_per_launch": bpc * ncell},
         "per_quadrature": {q: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                            | {"roofline_frac": round(r["achieved_gbs"] / peak, 4)} for q, r in results.items()},
@@ -579,6 +597,8 @@ def main():
     ap.add_argument("--quad", default="D2Q36-GH")
     ap.add_argument("--also", default="D2Q37", help="second quadrature measured on the same grid ('' = none)")
     ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--n-eq", type=int, default=3)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--kn", type=float, default=0.1)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-rows", type=int, default=48)

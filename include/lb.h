@@ -69,8 +69,9 @@ typedef enum {
 } lb_quadrature;
 
 /* Storage of the populations.  F32/F64 store the deviation f~ - w rho0;
- * BF16/F16 store (f~ - w rho0) / (w S) with a per-handle scale S.  The
- * arithmetic is FP32 for F32/BF16/F16 and FP64 for F64. */
+ * BF16/F16 store (f~ - w rho0) / s_a, s_a the power of two nearest w_a S for a
+ * per-handle scale S (so that the load and store scales are exact inverses),
+ * rounded stochastically.  The arithmetic is FP32 for F32/BF16/F16 and FP64 for F64. */
 typedef enum { LB_F32 = 0, LB_F64 = 1, LB_BF16 = 2, LB_F16 = 3 } lb_precision;
 
 /* How kn maps to the collision time tau of Eq. bgk.
@@ -88,7 +89,7 @@ typedef struct {
     double cfl;                /* off-lattice only: dt = cfl dx / max|xi_x|, 0 < cfl <= 1 (default 1) */
     int isothermal;            /* 1: T = 1 in the equilibrium (default 0: kinetic T) */
     int diag_capacity;         /* records kept in the device ring (default 65536) */
-    double storage_scale;      /* 16-bit scale S; 0 = set at init from the amplitude */
+    double storage_scale;      /* 16-bit scale S (rounded to a power of two); 0 = 2 x the initial amplitude */
     int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel
                                   (LB_ERR_UNSUPPORTED if not built for the storage).  Both give
                                   bitwise-identical results. */
@@ -97,6 +98,14 @@ typedef struct {
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
     void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
     void *alloc_ctx;
+    /* body force driving the standing shear wave (Sec. 4, Eq. force, turned so that the
+     * flow is along y): g = (0, g_y), g_y(x_i, t) = force_amp sin(x_i) cos(force_freq t).
+     * It enters the moments (rho u_y = sum xi_y f~ + rho g_y dt/2, Sec. 2.2) and the
+     * collision through the Hermite force term of Sec. 2.1 (Eq. 2order).  Reported
+     * u_y, momentum and sigma_xy are those of the forced scheme.  Forced steps run the
+     * plain-load kernel (step_kernel 2 is LB_ERR_UNSUPPORTED).  0 (default): free wave. */
+    double force_amp;
+    double force_freq;
 } lb_params;
 
 /* One diagnostics record per time level n (t = n dt), FP64 sums over the grid:
@@ -194,9 +203,10 @@ lb_status lb_quadrature_info(lb_quadrature quad, int *q, int *degree, double *xi
  * added and removed between runs (continuous batching); admission is by the
  * device-memory budget of the batch arena.  Lax-Wendroff product sets only.
  * Each instance starts from the shear wave u_y = u0 sin(x_i) (rho = T = 1) and
- * records A(n), S(n) (as in lb_diag) for every level it processes.  The per-cell
- * arithmetic is the single-lattice one: an instance's populations are bitwise
- * the same alone or in any mix, and bitwise those of an lb_handle run (F32).
+ * records A(n), S(n) (as in lb_diag, summed in FP32) for every level it
+ * processes.  The per-cell arithmetic is the single-lattice one (the same
+ * collision function): an instance's results are bitwise the same alone or in
+ * any mix, and agree with an lb_handle run of the same problem to FP32 rounding.
  * ------------------------------------------------------------------------- */
 typedef struct lb_batch lb_batch;
 

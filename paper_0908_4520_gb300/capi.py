@@ -41,6 +41,7 @@ class lb_params(ctypes.Structure):
         ("cfl", ctypes.c_double), ("isothermal", ctypes.c_int), ("diag_capacity", ctypes.c_int),
         ("storage_scale", ctypes.c_double), ("step_kernel", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
+        ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double),
     ]
 
 

@@ -176,10 +176,14 @@ struct lb_handle {
         A.x0_last = tma ? tma_x0_last : x0_last;
         A.isothermal = p.isothermal;
         A.diag_every = 1;
-        A.omega = (R)omega;
+        const double om = std::is_same<R, float>::value ? lbh::snap_unit(omega) : omega;
+        A.omega = (R)om;
         A.rho0 = (R)1.0;
-        A.sigma_fac = (R)(1.0 - 0.5 * omega);
+        A.sigma_fac = (R)(1.0 - 0.5 * om);
+        A.tau = (R)tau;
         A.dt = dt;
+        A.force_amp = p.force_amp;
+        A.force_freq = p.force_freq;
         A.sinx = static_cast<const R*>(sin_d);
         A.cosx = static_cast<const R*>(cos_d);
         A.partials = partials;
@@ -246,6 +250,8 @@ lb_status launch_any(lb_handle* h, int kind, const void* src, void* dst, int raw
 
 // One step launch: level n -> n+1 (src = buf[cur] holds f*(n-1), dst gets f*(n)).
 lb_status step_once(lb_handle* h, int from) {
+    if (h->p.force_amp != 0.0)  // the forced step runs the plain-load kernel
+        return launch_any(h, lbk::kStepForced, h->buf[from], h->buf[1 - from], 0, h->grid);
     if (h->use_tma) return launch_any(h, lbk::kStepTma, h->buf[from], h->buf[1 - from], 0, h->tma_grid);
     return launch_any(h, lbk::kStep, h->buf[from], h->buf[1 - from], 0, h->grid);
 }
@@ -304,7 +310,7 @@ lb_status set_scale_and_tables(lb_handle* h, double amp) {
     if (h->p.precision == LB_BF16 || h->p.precision == LB_F16) {
         double s = h->p.storage_scale;
         if (s <= 0) s = std::max(2.0 * amp, 1e-6);
-        h->scale = s;
+        h->scale = lbh::pow2_near(s);
     } else {
         h->scale = 1.0;
     }
@@ -328,7 +334,7 @@ lb_status init_common(lb_handle* h, double u0, double u1, const double* d_rho, c
                               nullptr, nullptr, nullptr, u0, u1, d_rho, d_ux, d_uy, d_T);
     if (st != LB_OK) return st;
     // level 0: collide f~(0) (no streaming) -> f*(0) in buf[0], record 0
-    st = launch_any(h, lbk::kStep, h->buf[1], h->buf[0], 1, h->grid);
+    st = launch_any(h, h->p.force_amp != 0.0 ? lbk::kStepForced : lbk::kStep, h->buf[1], h->buf[0], 1, h->grid);
     if (st != LB_OK) return st;
     h->cur = 0;
     h->raw_prev = true;
@@ -358,6 +364,8 @@ void lb_params_default(lb_params* p) {
     p->diag_capacity = 65536;
     p->storage_scale = 0.0;
     p->step_kernel = 0;
+    p->force_amp = 0.0;
+    p->force_freq = 0.0;
 }
 
 const char* lb_status_string(lb_status s) {
@@ -430,6 +438,8 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     if (P.kn_convention != LB_KN_LAMBDA && P.kn_convention != LB_KN_PAPER)
         return reject(LB_ERR_ARG, "unknown kn_convention");
     if (P.step_kernel < 0 || P.step_kernel > 2) return reject(LB_ERR_ARG, "step_kernel must be 0, 1 or 2");
+    if (!std::isfinite(P.force_amp) || !std::isfinite(P.force_freq))
+        return reject(LB_ERR_ARG, "force_amp and force_freq must be finite");
 
     lb_handle* h = new (std::nothrow) lb_handle();
     if (!h) return reject(LB_ERR_NOMEM, "host allocation");
@@ -496,7 +506,11 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         return reject(LB_ERR_CUDA, "no CUDA device");
     }
     const int occ = std::max(1, h->shape.occupancy);
-    if (h->shape.tma) {
+    if (P.force_amp != 0.0 && P.step_kernel == 2) {
+        delete h;
+        return reject(LB_ERR_UNSUPPORTED, "the TMA-staged step kernel runs the free wave; forced runs use the plain kernel");
+    }
+    if (h->shape.tma && P.force_amp == 0.0) {
         const int ttw = 32 * h->shape.tma_V;
         h->tma_ntiles_x = (P.nx + ttw - 1) / ttw;
         h->tma_x0_last = P.nx >= ttw ? P.nx - ttw : 0;

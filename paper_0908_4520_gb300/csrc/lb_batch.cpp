@@ -331,10 +331,10 @@ lb_status lb_batch_add(lb_batch* b, const lb_instance_desc* d, int* slot) {
     for (double a : vs.axis) amax = std::max(amax, std::fabs(a));
     const double dt = dx / amax;
     const double tau = b->p.kn_convention == LB_KN_LAMBDA ? d->kn * std::sqrt(2.0 / M_PI) : d->kn;
-    const double omega = dt / (tau + 0.5 * dt);
+    const double omega = lbh::snap_unit(dt / (tau + 0.5 * dt));
     in.omega = (float)omega;
     in.sigma_fac = (float)(1.0 - 0.5 * omega);
-    in.scale = (float)std::max(2.0 * std::fabs(d->u0), 1e-6);
+    in.scale = (float)lbh::pow2_near(std::max(2.0 * std::fabs(d->u0), 1e-6));
     in.stop_ratio2 = (float)(d->stop_ratio * d->stop_ratio);
     in.h0 = 0.f;
     in.u0 = d->u0;

@@ -65,7 +65,10 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
     if (tid == 0) s_done = in.done;
     __syncthreads();
 
+    // 16-bit storage: deviation = stored * sc[a] * scale; sc (tables built with S = 1) and
+    // scale are powers of two, so the load and store scales are exact inverses
     const float scale = in.scale;
+    const float inv_scale = 1.0f / scale;
     for (; level <= stop && !s_done; ++level) {
         const S* src = buf[cur];
         S* dst = buf[level == 0 ? 0 : 1 - cur];
@@ -82,8 +85,8 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
                     constexpr int a = decltype(ac)::value;
                     if constexpr (Is16<S>::value) {
                         S tmp;
-                        st1<S, float>(&tmp, deq, 1.0f / (t.w[a] * scale));
-                        ft[a] = batch_load<S>(&tmp, t.w[a] * scale);
+                        st1<S, float>(&tmp, deq, t.scinv[a] * inv_scale);
+                        ft[a] = batch_load<S>(&tmp, t.sc[a] * scale);
                     } else {
                         ft[a] = deq;
                     }
@@ -94,7 +97,7 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
                 static_for<0, Q>([&](auto ac) {
                     constexpr int a = decltype(ac)::value;
                     constexpr int ix = VS::ix(a), iy = VS::iy(a);
-                    const float sc = Is16<S>::value ? t.w[a] * scale : 1.f;
+                    const float sc = Is16<S>::value ? t.sc[a] * scale : 1.f;
                     const S* pl = src + (long long)a * ncell;
                     const float ly0 = t.lw[iy][0], ly1 = t.lw[iy][1], ly2 = t.lw[iy][2];
                     const float lx0 = t.lw[ix][0], lx1 = t.lw[ix][1], lx2 = t.lw[ix][2];
@@ -107,14 +110,14 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
                 });
             }
             const CellOut<float> co = collide_cell<VS, N, float, float, true>(
-                t, 1.f, omega, sigma_fac, in.isothermal, true,
+                t, 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
                 [&](auto ac) -> float& { return ft[decltype(ac)::value]; });
             uint32_t r = Is16<S>::value ? sr_seed(level, c) : 0u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                if constexpr (Is16<S>::value) r = xorshift32(r);
+                if constexpr (Is16<S>::value) r = sr_next(r);
                 dst[(long long)a * ncell + c] =
-                    to_storage<S, float>(ft[a], Is16<S>::value ? 1.0f / (t.w[a] * scale) : 1.f, r);
+                    to_storage<S, float>(ft[a], Is16<S>::value ? t.scinv[a] * inv_scale : 1.f, r);
             }
             pa = fma(co.uy, sinx[x], pa);
             ps = fma(co.sig, cosx[x], ps);

@@ -20,7 +20,7 @@ struct BatchInst {
     int status;           // bit 0: non-finite
     int isothermal;
     float omega, sigma_fac;
-    float scale;          // 16-bit storage: deviation = stored * w * scale
+    float scale;          // 16-bit storage: deviation = stored * sc[a] * scale (powers of two)
     float stop_ratio2;    // stop once H <= stop_ratio2 * H0 (0: never)
     float h0;             // H at level 0
     float pad;

@@ -36,7 +36,7 @@ struct Tab {
     R scinv[kMaxQ];           // 16-bit storage: stored = deviation / (w S)
 };
 
-enum Kind : int { kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kQueryShape = -1 };
+enum Kind : int { kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kStepForced = 4, kQueryShape = -1 };
 
 // Population layout: plane a, row y, column x at
 //   a * plane + origin + y * pitch + x,   origin = gy * pitch + kGhostX,
@@ -58,7 +58,10 @@ struct Args {
     int diag_every;           // record diagnostics when level % diag_every == 0
     R omega, rho0;
     R sigma_fac;              // 1 - omega / 2
+    R tau;                    // collision time of Eq. bgk
     double dt;
+    double force_amp;         // body force g_y = force_amp sin(x_i) cos(force_freq t); 0: none
+    double force_freq;
     const R* sinx;            // sin(x_i), nx entries
     const R* cosx;            // cos(x_i)
     double* partials;         // gridDim.x * kDiagSlots

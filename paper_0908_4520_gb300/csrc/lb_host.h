@@ -1,7 +1,9 @@
 // Host-side builder declarations (quadrature, step constants).
 #pragma once
 
+#include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lb.h"
@@ -32,6 +34,19 @@ double hermite_he(int k, double x);
 // Message returned by lb_last_error(NULL) on this thread.
 void set_last_error(const std::string& m);
 
+// Power of two nearest v > 0 (16-bit storage scales: exact inverses in FP32).
+inline double pow2_near(double v) { return std::exp2(std::nearbyint(std::log2(v))); }
+
+// FP32 constants that must sum to exactly one with their complement (the relaxation
+// weight omega and 1 - omega, the three Lax-Wendroff weights) are rounded to a
+// multiple of 2^-24 (2^-23 at or above 1): then 1 - v is exact in FP32 and no step
+// scales the conserved moments by a fixed rounding bias.  The change of v is below
+// 6e-8, far inside the FP32 error of the step.
+inline double snap_unit(double v) {
+    const double q = std::fabs(v) >= 1.0 ? 8388608.0 : 16777216.0;
+    return std::nearbyint(v * q) / q;
+}
+
 // Kernel tables of a velocity set (FP64 on the host, rounded once to R):
 // axis nodes, He_k(a_i)/k!, Lax-Wendroff weights for Courant numbers a_i dt/dx,
 // weights and their inverses, xi_x xi_y, |xi|^2, 16-bit storage scales w S.
@@ -52,17 +67,26 @@ void build_tab(const VelocitySetInfo& vs, double dt, double dx, double scale, lb
             t.whn[i][k] = (R)(wm[i] * hermite_he(k, vs.axis[i]) / fact);
         }
         const double C = vs.on_lattice ? 0.0 : vs.axis[i] * dt / dx;
-        t.lw[i][0] = (R)(0.5 * C * (1.0 + C));
-        t.lw[i][1] = (R)(1.0 - C * C);
-        t.lw[i][2] = (R)(-0.5 * C * (1.0 - C));
+        double l0 = 0.5 * C * (1.0 + C), l2 = -0.5 * C * (1.0 - C);
+        if (std::is_same<R, float>::value) {  // weights summing to one exactly in FP32
+            l0 = snap_unit(l0);
+            l2 = snap_unit(l2);
+        }
+        t.lw[i][0] = (R)l0;
+        t.lw[i][1] = (R)(1.0 - l0 - l2);
+        t.lw[i][2] = (R)l2;
     }
     for (int a = 0; a < vs.q; ++a) {
         t.w[a] = (R)vs.w[a];
         t.winv[a] = (R)(1.0 / vs.w[a]);
         t.xixy[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a + 1]);
         t.xi2[a] = (R)(vs.xi[2 * a] * vs.xi[2 * a] + vs.xi[2 * a + 1] * vs.xi[2 * a + 1]);
-        t.sc[a] = (R)(vs.w[a] * scale);
-        t.scinv[a] = (R)(1.0 / (vs.w[a] * scale));
+        // 16-bit storage scale of velocity a: the power of two nearest w_a S, so that
+        // stored = deviation * scinv and deviation = stored * sc are exact inverses (a
+        // product sc * scinv != 1 would scale every population by a fixed bias per step)
+        const double p2 = pow2_near(vs.w[a] * scale);
+        t.sc[a] = (R)p2;
+        t.scinv[a] = (R)(1.0 / p2);
     }
 }
 

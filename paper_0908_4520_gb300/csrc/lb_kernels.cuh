@@ -174,8 +174,9 @@ __device__ __forceinline__ R store_scale(const Tab<R>& t, int a) {
 // value equals the FP32 value in expectation), so per-step changes smaller than
 // half a 16-bit ulp are not rounded away (the decay would stagnate).  The random
 // bits come from a counter-based generator: MurmurHash3's 32-bit finalizer of
-// (cell, level) seeds one xorshift32 stream per cell, advanced once per
-// velocity, so the result does not depend on the launch geometry.
+// (cell, level) seeds one 32-bit linear congruential stream per cell (multiplier
+// 1664525, increment 1013904223), advanced once per velocity; its high bits are
+// the rounding bits.  The result does not depend on the launch geometry.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -184,28 +185,43 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ uint32_t xorshift32(uint32_t x) {
-    x ^= x << 13;
-    x ^= x >> 17;
-    x ^= x << 5;
-    return x;
-}
+__device__ __forceinline__ uint32_t sr_next(uint32_t x) { return x * 1664525u + 1013904223u; }
 __device__ __forceinline__ uint32_t sr_seed(long long level, long long cell) {
     return fmix32((uint32_t)cell ^ fmix32((uint32_t)level * 0x9e3779b9u + 0x7f4a7c15u));
 }
+// random bits below the 16-bit mantissa of an FP32 value: 13 for FP16, 16 for BF16
+template <class S>
+__device__ __forceinline__ uint32_t sr_bits(uint32_t r) {
+    return std::is_same<S, __half>::value ? (r >> 19) : (r >> 16);
+}
 
-// storage value of a deviation (16-bit: stochastic rounding with the random bits r)
+// storage value of a deviation (16-bit: stochastic rounding with the random bits of r)
 template <class S, class R>
 __device__ __forceinline__ S to_storage(R v, R scinv, uint32_t r) {
     if constexpr (std::is_same<S, __half>::value) {
-        return __float2half_rz(__uint_as_float(__float_as_uint(v * scinv) + (r & 0x1fffu)));
+        return __float2half_rz(__uint_as_float(__float_as_uint(v * scinv) + sr_bits<S>(r)));
     } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
-        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v * scinv) + (r & 0xffffu)));
+        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v * scinv) + sr_bits<S>(r)));
     } else {
         (void)scinv;
         (void)r;
         return v;
     }
+}
+
+// Two scaled values (already multiplied by the storage scale) rounded stochastically
+// into one 16-bit pair word, the first in the low half (one conversion instruction).
+template <class S>
+__device__ __forceinline__ uint32_t to_storage16x2(float h0, float h1, uint32_t r0, uint32_t r1) {
+    const float a = __uint_as_float(__float_as_uint(h0) + sr_bits<S>(r0));
+    const float b = __uint_as_float(__float_as_uint(h1) + sr_bits<S>(r1));
+    uint32_t d;
+    if constexpr (std::is_same<S, __half>::value) {
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    } else {
+        asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    }
+    return d;
 }
 
 template <class S>
@@ -352,17 +368,25 @@ struct Pack<float, 2> {
 #ifndef LB_CFG_V
 #define LB_CFG_V 2
 #endif
+#ifndef LB_CFG_V_LARGEQ
+#define LB_CFG_V_LARGEQ 2  // cells per thread of the plain kernel for q > 40
+#endif
+#ifndef LB_TMA_V
+#define LB_TMA_V 2         // cells per thread of the TMA-staged kernel (FP32/16-bit storage)
+#endif
 #ifndef LB_CFG_ROWS
 #define LB_CFG_ROWS 8
 #endif
 #ifndef LB_CFG_MINB
 #define LB_CFG_MINB 1
 #endif
+// TMA-staged step kernel: consumer rows per tile (q <= 40) and velocities per stage
+// (0: 6 for Lax-Wendroff sets, 4 for exact-shift sets), from a sweep at 4096^2
 #ifndef LB_TMA_ROWS
-#define LB_TMA_ROWS 8
+#define LB_TMA_ROWS 11
 #endif
 #ifndef LB_TMA_K
-#define LB_TMA_K 4
+#define LB_TMA_K 0
 #endif
 #ifndef LB_TMA_SMEM
 #define LB_TMA_SMEM (200 * 1024)
@@ -373,7 +397,7 @@ struct Pack<float, 2> {
 
 template <class VS, class S>
 struct Cfg {
-    static constexpr int V = (sizeof(S) == 8 || VS::Q > 40) ? 1 : LB_CFG_V;
+    static constexpr int V = sizeof(S) == 8 ? 1 : (VS::Q > 40 ? LB_CFG_V_LARGEQ : LB_CFG_V);
     static constexpr int ROWS = LB_CFG_ROWS;
     static constexpr int THREADS = 32 * ROWS;
     static constexpr int MINB = LB_CFG_MINB;
@@ -381,10 +405,10 @@ struct Cfg {
 
 template <class VS, class S>
 struct TmaCfg {
-    static constexpr int V = (sizeof(S) == 8) ? 1 : 2;
+    static constexpr int V = (sizeof(S) == 8) ? 1 : LB_TMA_V;
     // consumer warps: with the producer warp, 8 warps leave 255 registers a thread
-    // (two warps per SM sub-partition) for the 2 x 64 populations of D2Q64; 9 warps
-    // cap a thread at 168 registers, enough for q <= 37
+    // (two warps per SM sub-partition) for the 2 x 64 populations of D2Q64; 9 to 12
+    // warps cap a thread at 168 registers, enough for q <= 37
     static constexpr int ROWS = VS::Q > 40 ? 7 : LB_TMA_ROWS;
     static constexpr int TW = 32 * V;
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
@@ -395,13 +419,17 @@ struct TmaCfg {
     // stride of the velocity slots in a stage: dense for one 3-D box (Lax-Wendroff),
     // 128-byte aligned for separate boxes (exact shift)
     static constexpr int SLOT = LW ? BOX : ((BOX * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
-    static constexpr int K = LB_TMA_K;                  // velocities per stage
+    static constexpr int K = LB_TMA_K > 0 ? LB_TMA_K : (LW ? 6 : 4);  // velocities per stage
     static constexpr int NG = (VS::Q + K - 1) / K;      // stages per tile
     static constexpr int STAGE_BYTES = (K * SLOT * (int)sizeof(S) + 127) / 128 * 128;
     static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
     static constexpr int NS = NS_FIT < 2 * NG ? NS_FIT : 2 * NG;
     static constexpr int THREADS = 32 * (ROWS + 1);     // + one producer warp
-    static constexpr int MAXREG = (ROWS + 1) <= 8 ? 255 : 168;
+    // registers a thread may hold: each SM sub-partition's 16384 registers are shared by
+    // ceil(warps / 4) warps of the block (255 for 8 warps, 168 for 9..12, 128 for 13..16)
+    static constexpr int WARPS_PER_SMSP = (ROWS + 1 + 3) / 4;
+    static constexpr int MAXREG_FIT = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
+    static constexpr int MAXREG = MAXREG_FIT > 255 ? 255 : MAXREG_FIT;
     static constexpr int SMEM = NS * STAGE_BYTES + 2 * NS * 8 + 128;  // + alignment slack
     static constexpr int BOX_D = LW ? K : 1;            // velocities per TMA box
 };
@@ -557,9 +585,14 @@ struct CellOut {
 //    weights w_a = W_ix W_iy the weights fold into the per-axis factors, so
 //    omega (f^eq_a - w_a rho0) = sum_{ky<=N} PX[ix][ky] QY[iy][ky]
 //  * relaxation (Eq. 2order): f* = (1 - omega) f~ + omega f^eq, one FMA a velocity
+//  * body force g = (0, g) (Secs. 2.1, 2.2; forced): rho u_y = sum xi_y f~ + rho g dt/2,
+//    2 rho T gains dt rho g u_y, sigma_xy gains (dt/2) rho g u_x (the xy moment of
+//    the force term), and the force term relaxed with weight omega tau,
+//    omega tau g_a = omega w_a rho g sum_{ky>=1} c_kx c_{ky-1} He_kx He_ky / (kx! (ky-1)!),
+//    folds into the y factors: c_ky -> c_ky + ky tau g c_{ky-1} (ky >= 1)
 template <class VS, int N, class R, class T, bool COLLIDE, class F>
 __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R omega, R sigma_fac, int isothermal,
-                                                   bool diag, F&& f) {
+                                                   bool diag, bool forced, T gf, R tau, R dt, F&& f) {
     constexpr int NA = VS::NA;
     const T zero = vsplat<T>(R(0));
     T C[NA], Ry[NA];
@@ -596,18 +629,26 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
         for (int i = 0; i < NA; ++i) pxy = vfma(vsplat<T>(t.a[i]), P[i], pxy);
     }
     const T rho = vadd(vsplat<T>(rho0), drho);
+    const T rg = forced ? vmul(rho, gf) : zero;  // rho g
+    if (forced) jy = vfma(vsplat<T>(R(0.5) * dt), rg, jy);
     const T inv = vrcp(rho);
     const T ux = vmul(jx, inv), uy = vmul(jy, inv);
     const T u2 = vfma(ux, ux, vmul(uy, uy));
     T th = zero;
-    if (!isothermal) th = vmul(vmul(vsub(vsub(en, vadd(drho, drho)), vmul(rho, u2)), vsplat<T>(R(0.5))), inv);
+    if (!isothermal) {
+        T e2 = vsub(vsub(en, vadd(drho, drho)), vmul(rho, u2));
+        if (forced) e2 = vfma(vmul(vsplat<T>(dt), rg), uy, e2);
+        th = vmul(vmul(e2, vsplat<T>(R(0.5))), inv);
+    }
     o.drho = drho;
     o.jx = jx;
     o.jy = jy;
     o.ux = ux;
     o.uy = uy;
     o.th = th;
-    o.sig = vmul(vsplat<T>(sigma_fac), vsub(pxy, vmul(rho, vmul(ux, uy))));
+    T pneq = vsub(pxy, vmul(rho, vmul(ux, uy)));
+    if (forced) pneq = vfma(vmul(vsplat<T>(R(0.5) * dt), rg), ux, pneq);
+    o.sig = vmul(vsplat<T>(sigma_fac), pneq);
     o.h = h;
     if constexpr (COLLIDE) {
         // Hermite coefficients of the Maxwellian, c_{k+1} = u c_k + k (T - 1) c_{k-1}
@@ -620,6 +661,11 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
             const T kth = vmul(vsplat<T>(R(k)), th);
             cx[k + 1] = vfma(ux, cx[k], vmul(kth, cx[k - 1]));
             cy[k + 1] = vfma(uy, cy[k], vmul(kth, cy[k - 1]));
+        }
+        if (forced) {
+            const T tg = vmul(vsplat<T>(tau), gf);
+#pragma unroll
+            for (int k = N; k >= 1; --k) cy[k] = vfma(vmul(vsplat<T>(R(k)), tg), cy[k - 1], cy[k]);
         }
         T QY[NA][N + 1];
 #pragma unroll
@@ -678,16 +724,38 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
     return o;
 }
 
+// Amplitude A_f cos(phi n dt) of the body force at time level n (0 when unforced).
+template <class R>
+__device__ __forceinline__ R force_at_level(const Args<R>& A, long long lvl) {
+    return A.force_amp != 0.0 ? (R)(A.force_amp * cos(A.force_freq * (double)lvl * A.dt)) : R(0);
+}
+
 // Collision and store (or the moment outputs) of the V cells (g.x .., y) whose
 // streamed populations are in ft.  Diagnostics are reduced over the warp in
 // FP32 and added to acc (lane 0) in FP64.
 template <class VS, int N, class S, class R, int V, int KIND, class T>
 __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], S* __restrict__ dst, int y,
-                                              const Lane& g, bool diag, double (&acc)[6], int lane, long long lvl) {
+                                              const Lane& g, bool diag, double (&acc)[6], int lane, long long lvl,
+                                              R gt) {
     constexpr int Q = VS::Q;
-    const CellOut<T> co = collide_cell<VS, N, R, T, KIND == kStep>(
-        A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments,
-        [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
+    // body force g_y(x_i, t_n) = gt sin(x_i), gt = A_f cos(phi t_n) (driven standing wave, Sec. 4);
+    // compiled out of the unforced step kernels
+    constexpr bool STEP = (KIND == kStep || KIND == kStepForced);
+    const bool forced = (KIND != kStep) && A.force_amp != 0.0;
+    T gf = vsplat<T>(R(0));
+    if (forced) {
+        R gl[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) gl[k] = gt * A.sinx[min(g.x + k, A.nx - 1)];
+        if constexpr (V == 2) {
+            gf = pack_lanes<T, R>(gl[0], gl[1]);
+        } else {
+            gf = gl[0];
+        }
+    }
+    const CellOut<T> co = collide_cell<VS, N, R, T, STEP>(
+        A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
+        (R)A.dt, [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
     if constexpr (KIND == kMoments) {
         if (g.own) {
             static_for<0, V>([&](auto kc) {
@@ -707,7 +775,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             });
         }
     }
-    if constexpr (KIND == kStep) {
+    if constexpr (STEP) {
         if (g.own) {
             S* base = dst + A.origin + (long long)y * A.pitch + g.x;
             uint32_t r0 = 0, r1 = 0;
@@ -720,15 +788,21 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
                 constexpr int a = decltype(ac)::value;
                 const R si = store_scale<S, R>(A.tab, a);
                 if constexpr (Is16<S>::value) {
-                    r0 = xorshift32(r0);
-                    r1 = xorshift32(r1);
+                    r0 = sr_next(r0);
+                    r1 = sr_next(r1);
                 }
-                const S s0 = to_storage<S, R>(lane_get<0>(ft[a]), si, r0);
-                const S s1 = to_storage<S, R>(lane_get<V - 1>(ft[a]), si, r1);
-                if constexpr (V == 2) {
-                    store_raw2<S>(p, s0, s1);
+                if constexpr (Is16<S>::value && V == 2) {
+                    const T hs = vmul(ft[a], vsplat<T>(si));
+                    __stcs(reinterpret_cast<unsigned int*>(p),
+                           to_storage16x2<S>(lane_get<0>(hs), lane_get<1>(hs), r0, r1));
                 } else {
-                    store_raw<S>(p, s0);
+                    const S s0 = to_storage<S, R>(lane_get<0>(ft[a]), si, r0);
+                    const S s1 = to_storage<S, R>(lane_get<V - 1>(ft[a]), si, r1);
+                    if constexpr (V == 2) {
+                        store_raw2<S>(p, s0, s1);
+                    } else {
+                        store_raw<S>(p, s0);
+                    }
                 }
                 p += A.plane;
             });
@@ -824,6 +898,7 @@ __device__ __forceinline__ void finish_step(const Args<R>& A, const double (&acc
 
 // ------------------------------------------------------------ register kernel
 // KIND = kStep:    f* (next level) into dst, diagnostics when due.
+// KIND = kStepForced: the same with the body force (lb_params.force_amp != 0).
 // KIND = kMoments: per-cell rho, u, T, sigma_xy (and optionally f~) of the level; no store.
 template <class VS, int N, class S, class R, int KIND>
 __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
@@ -836,12 +911,19 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
     const S* __restrict__ src = static_cast<const S*>(A.src);
     S* __restrict__ dst = static_cast<S*>(A.dst);
 
+    constexpr bool STEP = (KIND == kStep || KIND == kStepForced);
     long long lvl = 0;
     bool diag = false;
-    if constexpr (KIND == kStep) {
+    if constexpr (STEP) {
         lvl = __ldcg(A.level);
         diag = (A.diag_every > 0) && (lvl % A.diag_every == 0);
+    } else {
+        // force phase of the state's level n: the device counter already points past it
+        // (the launch that produced f*(n) advanced it to n + 1)
+        if (A.force_amp != 0.0) lvl = __ldcg(A.level) - 1;
     }
+    R gt = R(0);
+    if constexpr (KIND != kStep) gt = force_at_level(A, lvl);
     double acc[6] = {0, 0, 0, 0, 0, 0};
 
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
@@ -890,36 +972,43 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
                 const S* r0 = pl + (long long)y * A.pitch;
                 const S* rm = r0 - A.pitch;
                 const S* rp = r0 + A.pitch;
-                R f0[V], fm[V], fp[V];
-                if constexpr (V == 2) {
-                    ld2<S, R>(r0 + g.xl, sc, f0[0], f0[1]);
-                    ld2<S, R>(rm + g.xl, sc, fm[0], fm[1]);
-                    ld2<S, R>(rp + g.xl, sc, fp[0], fp[1]);
-                } else {
-                    f0[0] = ld1<S, R>(r0 + g.xl, sc);
-                    fm[0] = ld1<S, R>(rm + g.xl, sc);
-                    fp[0] = ld1<S, R>(rp + g.xl, sc);
-                }
+                // the stencil is linear: 16-bit values are scaled once, after it (as in the
+                // TMA-staged kernel, so the two give the same bits)
+                const R one = R(1);
                 const int xe = (lane == 31) ? min(x0 + TW, A.nx) : x0 - 1;
-                const R ge = fma(ly0, ld1<S, R>(rm + xe, sc), fma(ly1, ld1<S, R>(r0 + xe, sc), ly2 * ld1<S, R>(rp + xe, sc)));
-                R gv[V];
-#pragma unroll
-                for (int k = 0; k < V; ++k) gv[k] = fma(ly0, fm[k], fma(ly1, f0[k], ly2 * fp[k]));
-                R gl = __shfl_up_sync(0xffffffffu, gv[V - 1], 1);
-                R gr = __shfl_down_sync(0xffffffffu, gv[0], 1);
-                gl = (lane == 0) ? ge : gl;
-                gr = (lane == 31) ? ge : gr;
+                const R ge = fma(ly0, ld1<S, R>(rm + xe, one), fma(ly1, ld1<S, R>(r0 + xe, one), ly2 * ld1<S, R>(rp + xe, one)));
                 if constexpr (V == 2) {
-                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1])),
-                                             fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr)));
+                    R a0v, a1v, b0v, b1v, c0v, c1v;
+                    ld2<S, R>(r0 + g.xl, one, a0v, a1v);
+                    ld2<S, R>(rm + g.xl, one, b0v, b1v);
+                    ld2<S, R>(rp + g.xl, one, c0v, c1v);
+                    const T gv = vfma(vsplat<T>(ly0), pack_lanes<T, R>(b0v, b1v),
+                                      vfma(vsplat<T>(ly1), pack_lanes<T, R>(a0v, a1v),
+                                           vmul(vsplat<T>(ly2), pack_lanes<T, R>(c0v, c1v))));
+                    const R gv0 = lane_get<0>(gv), gv1 = lane_get<1>(gv);
+                    R gl = __shfl_up_sync(0xffffffffu, gv1, 1);
+                    R gr = __shfl_down_sync(0xffffffffu, gv0, 1);
+                    gl = (lane == 0) ? ge : gl;
+                    gr = (lane == 31) ? ge : gr;
+                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv0, lx2 * gv1)),
+                                             fma(lx0, gv0, fma(lx1, gv1, lx2 * gr)));
                 } else {
-                    ft[a] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
+                    const R f0 = ld1<S, R>(r0 + g.xl, one);
+                    const R fm = ld1<S, R>(rm + g.xl, one);
+                    const R fp = ld1<S, R>(rp + g.xl, one);
+                    const R gv = fma(ly0, fm, fma(ly1, f0, ly2 * fp));
+                    R gl = __shfl_up_sync(0xffffffffu, gv, 1);
+                    R gr = __shfl_down_sync(0xffffffffu, gv, 1);
+                    gl = (lane == 0) ? ge : gl;
+                    gr = (lane == 31) ? ge : gr;
+                    ft[a] = fma(lx0, gl, fma(lx1, gv, lx2 * gr));
                 }
+                if constexpr (Is16<S>::value) ft[a] = vmul(ft[a], vsplat<T>(sc));
             }
         });
-        collide_store<VS, N, S, R, V, KIND>(A, ft, dst, y, g, diag, acc, lane, lvl);
+        collide_store<VS, N, S, R, V, KIND>(A, ft, dst, y, g, diag, acc, lane, lvl, gt);
     }
-    if constexpr (KIND == kStep) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
+    if constexpr (STEP) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
 }
 
 // ------------------------------------------------------------ TMA-staged step kernel
@@ -1067,7 +1156,9 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
         }
     } else {
         // ---------------- consumers: warp w owns row y0 + w of every tile
-        uint32_t it = 0;
+        // stage index and parity advance with the stream of groups (NG per tile)
+        int st_i = 0;
+        uint32_t st_ph = 0;
         for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
             const int ty = tile / A.ntiles_x;
             const int tx = tile - ty * A.ntiles_x;
@@ -1076,17 +1167,21 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             const int y = ty * ROWS + warp;
             const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
             using T = typename Pack<R, V>::T;
-        T ft[Q];
-            bool ok = true;
+            T ft[Q];
+            bool ok = !*abort_flag;
+            // Lax-Wendroff: column of this lane's first cell in the box row, and the column
+            // whose y-pass the two warp-edge lanes need (x0 - 1 for lane 0, x0 + TW for lane 31)
+            const int r_lw = (x0 - 1 + kGhostX) & (AL - 1);
+            const int c_lw = r_lw + 1 + lane * V;
+            const int ce_lw = (lane == 31) ? r_lw + 1 + TW : r_lw;
             static_for<0, NG>([&](auto gc) {
                 constexpr int grp = decltype(gc)::value;
-                const int s = (int)(it % NS);
                 if (ok) {
-                    ok = !*abort_flag && mbar_wait(&full[s], (it / NS) & 1u, A.status);
+                    ok = mbar_wait(&full[st_i], st_ph, A.status);
                     if (!ok) *abort_flag = 1;
                 }
                 if (ok) {
-                    const S* st = stages + (long long)s * STAGE_ELEMS;
+                    const S* st = stages + (long long)st_i * STAGE_ELEMS;
                     static_for<0, K>([&](auto jc) {
                         constexpr int j = decltype(jc)::value;
                         constexpr int a = grp * K + j;
@@ -1094,40 +1189,44 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                             const R sc = load_scale<S, R>(A.tab, a);
                             const S* box = st + j * SLOT;
                             if constexpr (C::LW) {
+                                // the stencil is linear: 16-bit values are scaled once, after it
+                                const R one = R(1);
                                 constexpr int ix = VS::ix(a), iy = VS::iy(a);
                                 const R ly0 = A.tab.lw[iy][0], ly1 = A.tab.lw[iy][1], ly2 = A.tab.lw[iy][2];
                                 const R lx0 = A.tab.lw[ix][0], lx1 = A.tab.lw[ix][1], lx2 = A.tab.lw[ix][2];
-                                const int r = (x0 - 1 + kGhostX) & (AL - 1);
                                 const S* rm = box + warp * BW;
                                 const S* r0 = rm + BW;
                                 const S* rp = r0 + BW;
-                                const int c = r + 1 + lane * V;
-                                R f0[V], fm[V], fp[V];
+                                const R ge = fma(ly0, sld1<S, R>(rm + ce_lw, one),
+                                                 fma(ly1, sld1<S, R>(r0 + ce_lw, one), ly2 * sld1<S, R>(rp + ce_lw, one)));
                                 if constexpr (V == 2) {
-                                    sld2<S, R>(r0 + c, sc, f0[0], f0[1]);
-                                    sld2<S, R>(rm + c, sc, fm[0], fm[1]);
-                                    sld2<S, R>(rp + c, sc, fp[0], fp[1]);
+                                    // y pass on the lane's two cells as one packed pair
+                                    R a0v, a1v, b0v, b1v, c0v, c1v;
+                                    sld2<S, R>(r0 + c_lw, one, a0v, a1v);
+                                    sld2<S, R>(rm + c_lw, one, b0v, b1v);
+                                    sld2<S, R>(rp + c_lw, one, c0v, c1v);
+                                    const T gv = vfma(vsplat<T>(ly0), pack_lanes<T, R>(b0v, b1v),
+                                                      vfma(vsplat<T>(ly1), pack_lanes<T, R>(a0v, a1v),
+                                                           vmul(vsplat<T>(ly2), pack_lanes<T, R>(c0v, c1v))));
+                                    const R gv0 = lane_get<0>(gv), gv1 = lane_get<1>(gv);
+                                    R gl = __shfl_up_sync(0xffffffffu, gv1, 1);
+                                    R gr = __shfl_down_sync(0xffffffffu, gv0, 1);
+                                    gl = (lane == 0) ? ge : gl;
+                                    gr = (lane == 31) ? ge : gr;
+                                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv0, lx2 * gv1)),
+                                                             fma(lx0, gv0, fma(lx1, gv1, lx2 * gr)));
                                 } else {
-                                    f0[0] = sld1<S, R>(r0 + c, sc);
-                                    fm[0] = sld1<S, R>(rm + c, sc);
-                                    fp[0] = sld1<S, R>(rp + c, sc);
+                                    const R f0 = sld1<S, R>(r0 + c_lw, one);
+                                    const R fm = sld1<S, R>(rm + c_lw, one);
+                                    const R fp = sld1<S, R>(rp + c_lw, one);
+                                    const R gv = fma(ly0, fm, fma(ly1, f0, ly2 * fp));
+                                    R gl = __shfl_up_sync(0xffffffffu, gv, 1);
+                                    R gr = __shfl_down_sync(0xffffffffu, gv, 1);
+                                    gl = (lane == 0) ? ge : gl;
+                                    gr = (lane == 31) ? ge : gr;
+                                    ft[a] = fma(lx0, gl, fma(lx1, gv, lx2 * gr));
                                 }
-                                const int ce = (lane == 31) ? r + 1 + TW : r;
-                                const R ge = fma(ly0, sld1<S, R>(rm + ce, sc),
-                                                 fma(ly1, sld1<S, R>(r0 + ce, sc), ly2 * sld1<S, R>(rp + ce, sc)));
-                                R gv[V];
-#pragma unroll
-                                for (int k = 0; k < V; ++k) gv[k] = fma(ly0, fm[k], fma(ly1, f0[k], ly2 * fp[k]));
-                                R gl = __shfl_up_sync(0xffffffffu, gv[V - 1], 1);
-                                R gr = __shfl_down_sync(0xffffffffu, gv[0], 1);
-                                gl = (lane == 0) ? ge : gl;
-                                gr = (lane == 31) ? ge : gr;
-                                if constexpr (V == 2) {
-                                    ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv[0], lx2 * gv[1])),
-                                                             fma(lx0, gv[0], fma(lx1, gv[1], lx2 * gr)));
-                                } else {
-                                    ft[a] = fma(lx0, gl, fma(lx1, gv[0], lx2 * gr));
-                                }
+                                if constexpr (Is16<S>::value) ft[a] = vmul(ft[a], vsplat<T>(sc));
                             } else {
                                 constexpr int ex = VS::ex(a);
                                 const int r = (x0 - ex + kGhostX) & (AL - 1);
@@ -1145,13 +1244,16 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                         }
                     });
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty[s]);
+                    if (lane == 0) mbar_arrive(&empty[st_i]);
                 }
-                ++it;
+                if (++st_i == NS) {
+                    st_i = 0;
+                    st_ph ^= 1u;
+                }
             });
             if (!ok) break;
             if (y >= A.ny) continue;
-            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl);
+            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
         }
     }
     __syncthreads();
@@ -1225,6 +1327,9 @@ cudaError_t launch_typed(const Launch& L) {
     switch (L.kind) {
         case kStep:
             lb_fused_kernel<VS, N, S, R, kStep><<<L.grid, C::THREADS, 0, L.stream>>>(A);
+            break;
+        case kStepForced:
+            lb_fused_kernel<VS, N, S, R, kStepForced><<<L.grid, C::THREADS, 0, L.stream>>>(A);
             break;
         case kMoments:
             lb_fused_kernel<VS, N, S, R, kMoments><<<L.grid, C::THREADS, 0, L.stream>>>(A);
