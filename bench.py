@@ -33,6 +33,22 @@ METRIC = "MLUPS (million lattice-cell updates per second), fused collide-stream 
 WORKLOAD = "standing shear wave 4096x4096, D2Q36-GH (Lax-Wendroff), N=3, FP32 deviations, Kn=0.1"
 
 
+def reduce_max_ms(ms, dist, device):
+    """The job's time: the slowest rank's (all-reduce MAX over ranks; ms itself at N = 1)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(cells_per_rank, world, steps, ms):
+    """Whole-job MLUPS of a weak-scaling run: every rank's cell updates over the job's time."""
+    return cells_per_rank * world * steps / (ms / 1e3) / 1e6
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -138,6 +154,32 @@ def kernel_label(args, tma):
     return f"lb_fused_kernel<{args.quad}, {args.n_eq}, {st}, kStep>"
 
 
+def dvm_crosscheck(capi, Lattice, args, n=256, t_end=6.0):
+    """Same-quadrature cross-check (Sec. 3.2): the lattice run of the benchmark's set on an
+    n x n subgrid (free wave u_y = 1e-3 sin x) against the GPU DVM with the same 1-D
+    Gauss-Hermite rule; max |A_LB - A_DVM| / U0 over t in [0, t_end]."""
+    import numpy as np
+
+    nodes = {"D2Q16-GH": 4, "D2Q36-GH": 6, "D2Q64-GH": 8}.get(args.quad)
+    if nodes is None:
+        return None
+    u0 = 1e-3
+    L = Lattice(args.quad, args.n_eq, n, n, args.kn, precision="f32", diag_capacity=1 << 14)
+    L.init_shear_wave(u0)
+    dt, tau = L.info["dt"], L.info["tau"]
+    L.step(int(t_end / dt))
+    rec = L.diagnostics()
+    L.close()
+    dt_dvm = 0.5 * (2 * np.pi / n) / float(np.max(np.abs(np.polynomial.hermite_e.hermegauss(nodes)[0])))
+    nd = int(t_end / dt_dvm) + 2
+    A, _ = capi.lb_dvm_run([tau], nodes, n, u0, nd)
+    td = dt_dvm * np.arange(nd + 1)
+    diff = float(np.max(np.abs(rec["amp"] - np.interp(rec["t"], td, A[0]))) / u0)
+    return {"grid": f"{n}x{n}", "kn": args.kn, "t_end": t_end, "max_abs_amp_diff_over_u0": round(diff, 7),
+            "dvm": f"GPU DVM, {nodes}-point Gauss-Hermite rule, nx {n}, cfl 0.5, FP64",
+            "lb": f"{args.quad} N={args.n_eq}, FP32"}
+
+
 def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32"):
     stream = torch.cuda.Stream()
     L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream)
@@ -193,11 +235,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if quad == args.quad:
             sampler.stop()
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max_ms(ev0.elapsed_time(ev1), dist, "cuda")
         if quad == args.quad:
             launches = L.launches - n0
         rec = L.diagnostics(4)
@@ -207,7 +245,7 @@ def run_gpu(args):
         per_launch_s = ms / 1e3 / args.steps
         results[quad] = {
             "ms_per_step": ms / args.steps,
-            "mlups": ncell * world * args.steps / (ms / 1e3) / 1e6,
+            "mlups": weak_value(ncell, world, args.steps, ms),
             "algorithmic_bytes_per_cell": bpc,
             "achieved_gbs": bpc * ncell / per_launch_s / 1e9,
             "finite": ok,
@@ -250,6 +288,7 @@ def run_gpu(args):
                "note": "timed: lb_init_fields from pinned host rho/ux/uy, steps each followed by a diagnostics "
                        "record read, final u_y read-back; bytes amortised per step"}
     L.close()
+    dvm = dvm_crosscheck(capi, Lattice, args) if rank == 0 else None
 
     if dist:
         dist.barrier()
@@ -290,6 +329,7 @@ def run_gpu(args):
         "per_quadrature": {q: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                            | {"roofline_frac": round(r["achieved_gbs"] / peak, 4)} for q, r in results.items()},
         "e2e": e2e,
+        "dvm_crosscheck": dvm,
         "gpu_launches": launches,
         "clocks": sampler.summary(),
         "cpu_baseline": cpu,

@@ -261,6 +261,24 @@ lb_status lb_batch_destroy(lb_batch *b);
 const char *lb_batch_last_error(const lb_batch *b);
 
 /* ---------------------------------------------------------------------------
+ * Discrete velocity method of Sec. 3.3: the reduced linearised BGK equation of the
+ * free standing shear wave (Eqs. LBGK, ga, gb, force zero),
+ *   dG/dt + xi_k dG/dx = (u - G)/tau,  u = sum_k w_k G_k,
+ * at the nodes xi_k of the n_nodes-point Gauss-Hermite rule, started from G = u0 sin x.
+ * Strang splitting of the exact relaxation around one Lax-Wendroff step,
+ * dt = cfl dx / max|xi_k|, dx = 2 pi / nx, FP64 on the GPU, one CTA per collision
+ * time.  For the same-quadrature cross-check of the lattice runs (Sec. 3.2).
+ *   tau          n_inst collision times (host array)
+ *   amp, shear   caller host arrays of n_inst x (nsteps + 1) doubles: A(n) and S(n)
+ *                (as in lb_diag, sigma = sum_k w_k xi_k G) of instance i at [i*(nsteps+1) + n]
+ *   stream       cudaStream_t (NULL = default); returns after the run.
+ * Errors: LB_ERR_ARG; LB_ERR_UNSUPPORTED if n_nodes x nx does not fit one CTA's shared
+ * memory (8 (n_nodes + 2) nx bytes); LB_ERR_NOMEM; LB_ERR_CUDA (lb_last_error(NULL)).
+ * ------------------------------------------------------------------------- */
+lb_status lb_dvm_run(int n_inst, const double *tau, int n_nodes, int nx, double cfl, double u0,
+                     int nsteps, double *amp, double *shear, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free solve of one small shear wave.  The paper has no
  * counterpart: this is an engineering entry point for callers that cannot
  * allocate device memory, e.g. a process whose free device memory is already

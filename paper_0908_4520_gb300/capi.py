@@ -152,6 +152,8 @@ def _load() -> ctypes.CDLL:
                                              ctypes.POINTER(ctypes.c_int)]),
         "lb_server_destroy": (ctypes.c_int, [H]),
         "lb_server_last_error": (ctypes.c_char_p, [H]),
+        "lb_dvm_run": (ctypes.c_int, [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_void_p]),
         "lb_solve_static": (ctypes.c_int, [ctypes.POINTER(lb_instance_desc), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                            ctypes.POINTER(lb_instance_state), ctypes.c_void_p]),
@@ -177,7 +179,7 @@ EXPORTS = [
     "lb_batch_run", "lb_batch_sync", "lb_batch_state", "lb_batch_history", "lb_batch_fit",
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
-    "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static",
+    "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static", "lb_dvm_run",
 ]
 
 
@@ -322,6 +324,17 @@ def lb_batch_add(b, d: lb_instance_desc) -> int:
     slot = ctypes.c_int()
     check_batch(lib.lb_batch_add(b, ctypes.byref(d), ctypes.byref(slot)), b)
     return slot.value
+
+
+def lb_dvm_run(taus, n_nodes: int, nx: int, u0: float, nsteps: int, cfl: float = 0.5, stream: int = 0):
+    """GPU DVM (Sec. 3.3) for each collision time in taus; returns (A, S) arrays of shape
+    (len(taus), nsteps + 1)."""
+    tau = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+    amp = np.empty((tau.size, nsteps + 1))
+    shear = np.empty((tau.size, nsteps + 1))
+    check(lib.lb_dvm_run(tau.size, _dptr(tau), n_nodes, nx, cfl, u0, nsteps, _dptr(amp), _dptr(shear),
+                         stream or None))
+    return amp, shear
 
 
 def lb_solve_static(desc: lb_instance_desc, precision: int = 0, kn_convention: int = 0, max_records: int = -1,

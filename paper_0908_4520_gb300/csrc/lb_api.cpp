@@ -511,7 +511,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         return reject(LB_ERR_UNSUPPORTED, "the TMA-staged step kernel runs the free wave; forced runs use the plain kernel");
     }
     if (h->shape.tma && P.force_amp == 0.0) {
-        const int ttw = 32 * h->shape.tma_V;
+        const int ttw = h->shape.tma_tw;
         h->tma_ntiles_x = (P.nx + ttw - 1) / ttw;
         h->tma_x0_last = P.nx >= ttw ? P.nx - ttw : 0;
         h->tma_ntiles = h->tma_ntiles_x * ((P.ny + h->shape.tma_rows - 1) / h->shape.tma_rows);

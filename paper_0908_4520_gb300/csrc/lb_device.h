@@ -88,6 +88,7 @@ struct Shape {
     // TMA-staged step kernel (0 = not built for this unit)
     int tma;
     int tma_V, tma_rows, tma_threads, tma_smem, tma_occupancy;
+    int tma_tw;     // cells a tile row produces (32 V, or 30 with halo lanes)
     int box_w, box_h, box_d;  // tensor-map box (x, y, velocities)
 };
 

@@ -362,17 +362,18 @@ struct Pack<float, 2> {
 };
 
 // ------------------------------------------------------------ configuration
-// Register kernel: cells per thread, rows per block, min resident blocks.
-// TMA kernel: consumer rows, velocities per stage, shared-memory budget.
-// Overridable at build time for tuning sweeps.
+// Launch shapes, from sweeps at 4096^2 (FP32, N = 3) and 2048^2 (D2Q64, N = 4):
+//  * Lax-Wendroff (Gauss-Hermite product) sets: one cell per lane and many warps
+//    (19 consumer rows, or 15 for q = 64), 6 velocities per TMA stage (12 for q = 64);
+//  * exact-shift sets: two cells per lane (packed f32x2), 11 consumer rows, 18
+//    velocities per stage.
+// The plain-load kernel takes the same cells per lane as the TMA-staged one, so the
+// two give the same bits.  Each value is overridable at build time (0 = the choice above).
 #ifndef LB_CFG_V
-#define LB_CFG_V 2
-#endif
-#ifndef LB_CFG_V_LARGEQ
-#define LB_CFG_V_LARGEQ 2  // cells per thread of the plain kernel for q > 40
+#define LB_CFG_V 0
 #endif
 #ifndef LB_TMA_V
-#define LB_TMA_V 2         // cells per thread of the TMA-staged kernel (FP32/16-bit storage)
+#define LB_TMA_V 0
 #endif
 #ifndef LB_CFG_ROWS
 #define LB_CFG_ROWS 8
@@ -380,13 +381,14 @@ struct Pack<float, 2> {
 #ifndef LB_CFG_MINB
 #define LB_CFG_MINB 1
 #endif
-// TMA-staged step kernel: consumer rows per tile (q <= 40) and velocities per stage
-// (0: 6 for Lax-Wendroff sets, 4 for exact-shift sets), from a sweep at 4096^2
 #ifndef LB_TMA_ROWS
-#define LB_TMA_ROWS 11
+#define LB_TMA_ROWS 0
 #endif
 #ifndef LB_TMA_K
 #define LB_TMA_K 0
+#endif
+#ifndef LB_TMA_HALO
+#define LB_TMA_HALO 1
 #endif
 #ifndef LB_TMA_SMEM
 #define LB_TMA_SMEM (200 * 1024)
@@ -395,9 +397,15 @@ struct Pack<float, 2> {
 #define LB_TMA_MINB 1
 #endif
 
+// cells per lane along x (FP64 storage: always 1)
+template <class VS, class S, int OVERRIDE>
+constexpr int cells_per_lane() {
+    return sizeof(S) == 8 ? 1 : (OVERRIDE > 0 ? OVERRIDE : (VS::kOnLattice ? 2 : 1));
+}
+
 template <class VS, class S>
 struct Cfg {
-    static constexpr int V = sizeof(S) == 8 ? 1 : (VS::Q > 40 ? LB_CFG_V_LARGEQ : LB_CFG_V);
+    static constexpr int V = cells_per_lane<VS, S, (LB_CFG_V > 0 ? LB_CFG_V : LB_TMA_V)>();
     static constexpr int ROWS = LB_CFG_ROWS;
     static constexpr int THREADS = 32 * ROWS;
     static constexpr int MINB = LB_CFG_MINB;
@@ -405,21 +413,21 @@ struct Cfg {
 
 template <class VS, class S>
 struct TmaCfg {
-    static constexpr int V = (sizeof(S) == 8) ? 1 : LB_TMA_V;
-    // consumer warps: with the producer warp, 8 warps leave 255 registers a thread
-    // (two warps per SM sub-partition) for the 2 x 64 populations of D2Q64; 9 to 12
-    // warps cap a thread at 168 registers, enough for q <= 37
-    static constexpr int ROWS = VS::Q > 40 ? 7 : LB_TMA_ROWS;
-    static constexpr int TW = 32 * V;
-    static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
     static constexpr bool LW = !VS::kOnLattice;
-    static constexpr int BW = LW ? TW + 2 * AL : TW + AL;
+    static constexpr int V = cells_per_lane<VS, S, LB_TMA_V>();
+    // consumer warps (+ one producer warp); the register cap follows from the count
+    static constexpr int ROWS = LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : 11);
+    static constexpr int TW = 32 * V;
+    static constexpr bool HALO = LB_TMA_HALO && LW && V == 1;  // edge lanes are halo lanes (30 cells a row)
+    static constexpr int TWO = HALO ? 30 : TW;           // cells a tile row produces
+    static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
+    static constexpr int BW = HALO ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
     static constexpr int BH = LW ? ROWS + 2 : ROWS;
     static constexpr int BOX = BW * BH;                 // elements of one velocity's box
     // stride of the velocity slots in a stage: dense for one 3-D box (Lax-Wendroff),
     // 128-byte aligned for separate boxes (exact shift)
     static constexpr int SLOT = LW ? BOX : ((BOX * (int)sizeof(S) + 127) / 128 * 128) / (int)sizeof(S);
-    static constexpr int K = LB_TMA_K > 0 ? LB_TMA_K : (LW ? 6 : 4);  // velocities per stage
+    static constexpr int K = LB_TMA_K > 0 ? LB_TMA_K : (LW ? (VS::Q > 40 ? 12 : 6) : 18);  // velocities per stage
     static constexpr int NG = (VS::Q + K - 1) / K;      // stages per tile
     static constexpr int STAGE_BYTES = (K * SLOT * (int)sizeof(S) + 127) / 128 * 128;
     static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
@@ -491,6 +499,17 @@ struct Lane {
     int xl;         // column read for the lane (x, or nx for lanes past the grid)
     bool own;       // x < nx and not a recomputed overlap cell
 };
+
+// TMA-staged Lax-Wendroff with one cell per lane: the warp's edge lanes are halo lanes
+// (columns x0 - 1 and x0 + 30), whose y-pass only feeds their neighbours' x-pass, so no
+// lane reads an extra column; lanes 1..30 own cells x0 .. x0 + 29.
+__device__ __forceinline__ Lane halo_lane_geometry(int lane, int x0, int tile_start, int nx) {
+    Lane g;
+    g.x = x0 - 1 + lane;
+    g.own = lane >= 1 && lane <= 30 && g.x < nx && g.x >= tile_start;
+    g.xl = g.x;
+    return g;
+}
 
 template <int V>
 __device__ __forceinline__ Lane lane_geometry(int lane, int x0, int tile_start, int nx) {
@@ -735,7 +754,7 @@ __device__ __forceinline__ R force_at_level(const Args<R>& A, long long lvl) {
 // FP32 and added to acc (lane 0) in FP64.
 template <class VS, int N, class S, class R, int V, int KIND, class T>
 __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], S* __restrict__ dst, int y,
-                                              const Lane& g, bool diag, double (&acc)[6], int lane, long long lvl,
+                                              const Lane& g, bool diag, R (&acc)[6], int lane, long long lvl,
                                               R gt) {
     constexpr int Q = VS::Q;
     // body force g_y(x_i, t_n) = gt sin(x_i), gt = A_f cos(phi t_n) (driven standing wave, Sec. 4);
@@ -746,7 +765,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     if (forced) {
         R gl[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) gl[k] = gt * A.sinx[min(g.x + k, A.nx - 1)];
+        for (int k = 0; k < V; ++k) gl[k] = gt * A.sinx[min(max(g.x + k, 0), A.nx - 1)];
         if constexpr (V == 2) {
             gf = pack_lanes<T, R>(gl[0], gl[1]);
         } else {
@@ -811,24 +830,18 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy)
                 rim_images<S, R, V>(A, dst, Q, g.x, y);
         }
-        if (diag) {
-            R v6[6] = {0, 0, 0, 0, 0, 0};
-            if (g.own) {
-                static_for<0, V>([&](auto kc) {
-                    constexpr int k = decltype(kc)::value;
-                    v6[0] += lane_get<k>(co.drho);
-                    v6[1] += lane_get<k>(co.jx);
-                    v6[2] += lane_get<k>(co.jy);
-                    v6[3] = fma(lane_get<k>(co.uy), A.sinx[g.x + k], v6[3]);
-                    v6[4] = fma(lane_get<k>(co.sig), A.cosx[g.x + k], v6[4]);
-                    v6[5] += lane_get<k>(co.h);
-                });
-            }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                const R sm = warp_sum(v6[i]);
-                if (lane == 0) acc[i] += (double)sm;
-            }
+        // per-thread partial sums over the thread's cells of every tile; reduced once per
+        // launch (warp, then FP64 across warps and blocks) in finish_step
+        if (diag && g.own) {
+            static_for<0, V>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                acc[0] += lane_get<k>(co.drho);
+                acc[1] += lane_get<k>(co.jx);
+                acc[2] += lane_get<k>(co.jy);
+                acc[3] = fma(lane_get<k>(co.uy), A.sinx[g.x + k], acc[3]);
+                acc[4] = fma(lane_get<k>(co.sig), A.cosx[g.x + k], acc[4]);
+                acc[5] += lane_get<k>(co.h);
+            });
         }
     }
 }
@@ -836,14 +849,17 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
 // End of a step launch: per-block FP64 partials, last-block fixed-order sum into
 // the diagnostics ring, level advance.  All threads of the block call it.
 template <class R, int NWARPS_DIAG>
-__device__ __forceinline__ void finish_step(const Args<R>& A, const double (&acc)[6], long long lvl, bool diag,
+__device__ __forceinline__ void finish_step(const Args<R>& A, const R (&acc)[6], long long lvl, bool diag,
                                             int warp, int lane) {
     __shared__ double red[NWARPS_DIAG][6];
     __shared__ bool is_last;
     __shared__ double tot[6];
-    if (diag && lane == 0 && warp < NWARPS_DIAG) {
+    if (diag) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) red[warp][i] = acc[i];
+        for (int i = 0; i < 6; ++i) {
+            const R sm = warp_sum(acc[i]);
+            if (lane == 0 && warp < NWARPS_DIAG) red[warp][i] = (double)sm;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -924,7 +940,7 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
     }
     R gt = R(0);
     if constexpr (KIND != kStep) gt = force_at_level(A, lvl);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    R acc[6] = {0, 0, 0, 0, 0, 0};
 
     for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int ty = tile / A.ntiles_x;
@@ -1027,8 +1043,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// try_wait with a suspend-time hint (ns): the waiting thread sleeps in hardware
-// instead of spinning (used by the producer, whose waits are not latency-critical)
+// try_wait with a suspend-time hint (ns): the waiting thread is suspended in hardware
+// until the phase completes or the hint runs out, instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -1043,6 +1059,7 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
     return ok != 0;
 }
 
+// try_wait with the default (system-dependent) suspend window: the consumers' fast path
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -1113,7 +1130,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
 
     const long long lvl = __ldcg(A.level);
     const bool diag = (A.diag_every > 0) && (lvl % A.diag_every == 0);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    R acc[6] = {0, 0, 0, 0, 0, 0};
     volatile int* abort_flag = &s_abort;
 
     if (warp == ROWS) {
@@ -1123,7 +1140,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             for (int tile = blockIdx.x; tile < A.ntiles && !*abort_flag; tile += gridDim.x) {
                 const int ty = tile / A.ntiles_x;
                 const int tx = tile - ty * A.ntiles_x;
-                const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tx * TW;
+                const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tx * C::TWO;
                 const int y0 = ty * ROWS;
                 for (int grp = 0; grp < NG; ++grp, ++it) {
                     const int s = (int)(it % NS);
@@ -1162,17 +1179,18 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
         for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
             const int ty = tile / A.ntiles_x;
             const int tx = tile - ty * A.ntiles_x;
-            const int tile_start = tx * TW;
+            const int tile_start = tx * C::TWO;
             const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
             const int y = ty * ROWS + warp;
-            const Lane g = lane_geometry<V>(lane, x0, tile_start, A.nx);
+            const Lane g = C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx)
+                                   : lane_geometry<V>(lane, x0, tile_start, A.nx);
             using T = typename Pack<R, V>::T;
             T ft[Q];
             bool ok = !*abort_flag;
             // Lax-Wendroff: column of this lane's first cell in the box row, and the column
             // whose y-pass the two warp-edge lanes need (x0 - 1 for lane 0, x0 + TW for lane 31)
             const int r_lw = (x0 - 1 + kGhostX) & (AL - 1);
-            const int c_lw = r_lw + 1 + lane * V;
+            const int c_lw = C::HALO ? r_lw + lane : r_lw + 1 + lane * V;
             const int ce_lw = (lane == 31) ? r_lw + 1 + TW : r_lw;
             static_for<0, NG>([&](auto gc) {
                 constexpr int grp = decltype(gc)::value;
@@ -1197,9 +1215,19 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                                 const S* rm = box + warp * BW;
                                 const S* r0 = rm + BW;
                                 const S* rp = r0 + BW;
-                                const R ge = fma(ly0, sld1<S, R>(rm + ce_lw, one),
-                                                 fma(ly1, sld1<S, R>(r0 + ce_lw, one), ly2 * sld1<S, R>(rp + ce_lw, one)));
-                                if constexpr (V == 2) {
+                                if constexpr (C::HALO) {
+                                    // y pass of the lane's column; x pass from the neighbours
+                                    const R f0 = sld1<S, R>(r0 + c_lw, one);
+                                    const R fm = sld1<S, R>(rm + c_lw, one);
+                                    const R fp = sld1<S, R>(rp + c_lw, one);
+                                    const R gv = fma(ly0, fm, fma(ly1, f0, ly2 * fp));
+                                    const R gl = __shfl_up_sync(0xffffffffu, gv, 1);
+                                    const R gr = __shfl_down_sync(0xffffffffu, gv, 1);
+                                    ft[a] = fma(lx0, gl, fma(lx1, gv, lx2 * gr));
+                                } else if constexpr (V == 2) {
+                                    const R ge = fma(ly0, sld1<S, R>(rm + ce_lw, one),
+                                                     fma(ly1, sld1<S, R>(r0 + ce_lw, one),
+                                                         ly2 * sld1<S, R>(rp + ce_lw, one)));
                                     // y pass on the lane's two cells as one packed pair
                                     R a0v, a1v, b0v, b1v, c0v, c1v;
                                     sld2<S, R>(r0 + c_lw, one, a0v, a1v);
@@ -1216,6 +1244,11 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                                     ft[a] = pack_lanes<T, R>(fma(lx0, gl, fma(lx1, gv0, lx2 * gv1)),
                                                              fma(lx0, gv0, fma(lx1, gv1, lx2 * gr)));
                                 } else {
+                                    // one cell per lane, all 32 lanes own cells: the edge lanes
+                                    // take their outer column's y pass from an extra read
+                                    const R ge = fma(ly0, sld1<S, R>(rm + ce_lw, one),
+                                                     fma(ly1, sld1<S, R>(r0 + ce_lw, one),
+                                                         ly2 * sld1<S, R>(rp + ce_lw, one)));
                                     const R f0 = sld1<S, R>(r0 + c_lw, one);
                                     const R fm = sld1<S, R>(rm + c_lw, one);
                                     const R fp = sld1<S, R>(rp + c_lw, one);
@@ -1314,6 +1347,7 @@ cudaError_t launch_typed(const Launch& L) {
             if (e != cudaSuccess) return e;
             sh->tma = sh->tma_occupancy > 0 ? 1 : 0;
             sh->tma_V = T::V;
+            sh->tma_tw = T::TWO;
             sh->tma_rows = T::ROWS;
             sh->tma_threads = T::THREADS;
             sh->tma_smem = T::SMEM;
