@@ -271,7 +271,7 @@ def run_gpu(args):
         import ctypes
 
         dptr = lambda t: ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))
-        e2e_steps = args.e2e_steps
+        e2e_steps = args.e2e_steps or args.steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         capi.check(capi.lib.lb_init_fields(L.h, dptr(rho_h), dptr(ux_h), dptr(uy_h), None), L.h)
@@ -285,8 +285,9 @@ def run_gpu(args):
         d2h = (64 * e2e_steps + 8 * ncell) / e2e_steps
         e2e = {"value": ncell * e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
-               "note": "timed: lb_init_fields from pinned host rho/ux/uy, steps each followed by a diagnostics "
-                       "record read, final u_y read-back; bytes amortised per step"}
+               "note": "timed: one solve through the C-ABI: lb_init_fields from pinned host rho/ux/uy, then "
+                       "the same number of levels as the device-timed run, each followed by a read of its "
+                       "diagnostics record, then the u_y field read back; bytes amortised per step"}
     L.close()
     dvm = dvm_crosscheck(capi, Lattice, args) if rank == 0 else None
 
@@ -533,6 +534,62 @@ def run_precision(args):
                                        "Kn log-uniform 0.01..10 (seed 9084520)"}})
 
 
+def run_driven(args):
+    """Driven standing shear wave (Sec. 4): body force g_y = A_f sin(x) cos(phi t), fluid at
+    rest at t = 0; amplitude |U|/A_f and phase lag of the periodic response of u_y for each
+    set and Kn, next to the Navier-Stokes and R13 closed forms (Kn = tau, the paper's Eq. KN)
+    and to the linearised scheme's response (which the runs must match)."""
+    import numpy as np
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_0908_4520_gb300 import Lattice
+
+    amp, phi, nx = 1e-4, 1.0, 64
+    kns = [0.01, 0.05, 0.1, 0.2, 0.5, 1.0]
+    sets = [("D2Q9", 2), ("D2Q16-GH", 2), ("D2Q16-GH", 3), ("D2Q36-GH", 3), ("D2Q64-GH", 4), ("D2Q37", 3)]
+    rows = []
+    t_wall = time.perf_counter()
+    cell_updates = 0
+    for quad, N in sets:
+        for kn in kns:
+            L = Lattice(quad, N, nx, 1, kn, precision="f64", kn_convention="paper", isothermal=True,
+                        force_amp=amp, force_freq=phi, diag_capacity=1 << 16)
+            L.init_shear_wave(0.0)
+            dt = L.info["dt"]
+            # the start-up transient decays at least as fast as the shear mode, exp(-kn t)
+            t_end = max(10.0 / kn, 30.0)
+            n = int(t_end / dt)
+            L.step(n)
+            rec = L.diagnostics()
+            L.close()
+            cell_updates += nx * n
+            t, A = rec["t"], rec["amp"]
+            sel = t >= t[-1] - 4 * np.pi / phi
+            X = np.stack([np.cos(phi * t[sel]), np.sin(phi * t[sel])], axis=1)
+            (a, b), *_ = np.linalg.lstsq(X, A[sel], rcond=None)
+            U = (a - 1j * b) / amp
+            ns = 1.0 / (1j * phi + kn)
+            i = 1j
+            num = 288 * kn**4 * i - 510 * phi * kn**3 + (520 * i - 225 * phi**2 * i) * kn**2 - 375 * phi * kn + 150 * i
+            den = (288 * phi * kn**4 + (510 * phi**2 * i - 270 * i) * kn**3 + (745 * phi - 225 * phi**3) * kn**2
+                   + (375 * phi**2 * i - 150 * i) * kn + 150 * phi)
+            r13 = -num / den
+            rows.append({"set": quad, "N": N, "kn": kn, "amplitude": round(abs(U), 6),
+                         "phase_lag": round(float(-np.angle(U)), 6),
+                         "ns": {"amplitude": round(abs(ns), 6), "phase_lag": round(float(-np.angle(ns)), 6)},
+                         "r13": {"amplitude": round(abs(r13), 6), "phase_lag": round(float(-np.angle(r13)), 6)},
+                         "levels": n})
+    wall = time.perf_counter() - t_wall
+    _common(args, "driven standing shear wave: amplitude and phase lag of u_y vs Kn (Sec. 4), LB on the GPU",
+            round(cell_updates / wall / 1e6, 3), "MLUPS", {
+                "dtype": "f64", "higher_is_better": True, "results": rows,
+                "config": {"workload": f"body force A_f sin x cos(phi t), A_f {amp}, phi {phi}, {nx}x1 periodic, "
+                                       "fluid at rest at t = 0, isothermal, Kn = tau; response fitted over the "
+                                       "last two periods", "wall_s": round(wall, 2)}})
+
+
 def run_serve(args):
     """Serving workload: seeded Poisson streams of shear-wave solves (10 % large 1024^2
     D2Q36-GH, FP16 deviation storage) replayed in real time through the request loop,
@@ -640,12 +697,12 @@ def main():
     ap.add_argument("--n-eq", type=int, default=3)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--kn", type=float, default=0.1)
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="levels of the end-to-end leg (0: --steps)")
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "precision", "serve"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "precision", "serve", "driven"])
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--requests-util", type=int, default=150)
     ap.add_argument("--rate", type=float, default=2000.0)
@@ -667,6 +724,8 @@ def main():
         run_precision(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "driven":
+        run_driven(args)
     else:
         run_gpu(args)
 

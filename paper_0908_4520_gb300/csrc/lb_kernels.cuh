@@ -387,8 +387,11 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_K
 #define LB_TMA_K 0
 #endif
+#ifndef LB_TMA_TILE_SYNC
+#define LB_TMA_TILE_SYNC -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
+#endif
 #ifndef LB_TMA_HALO
-#define LB_TMA_HALO 1
+#define LB_TMA_HALO -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
 #endif
 #ifndef LB_TMA_SMEM
 #define LB_TMA_SMEM (200 * 1024)
@@ -418,7 +421,14 @@ struct TmaCfg {
     // consumer warps (+ one producer warp); the register cap follows from the count
     static constexpr int ROWS = LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : 11);
     static constexpr int TW = 32 * V;
-    static constexpr bool HALO = LB_TMA_HALO && LW && V == 1;  // edge lanes are halo lanes (30 cells a row)
+    // Edge lanes as halo lanes (30 cells a row) and a per-tile barrier of the consumer warps,
+    // chosen per set and storage by the sweep at 4096^2 / 2048^2 (GLUPS, no halo / halo /
+    // halo + barrier): D2Q16 FP32 29.5 / 35.5 / 30.4; D2Q36 FP32 12.5 / 9.6 / 14.5; D2Q36
+    // 16-bit 12.1 / 15.9 / 14.4; D2Q64 FP32 5.38 / 4.95 / 4.97; D2Q64 16-bit 4.37 / 6.40 / 6.28.
+    static constexpr bool FP32_Q64 = sizeof(S) == 4 && VS::Q > 40;
+    static constexpr bool HALO = LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64));
+    static constexpr bool TILE_SYNC =
+        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && HALO && sizeof(S) == 4 && VS::Q == 36);
     static constexpr int TWO = HALO ? 30 : TW;           // cells a tile row produces
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
     static constexpr int BW = HALO ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
@@ -1284,9 +1294,16 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                     st_ph ^= 1u;
                 }
             });
+            if (ok && y < A.ny)
+                collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
+            if constexpr (C::TILE_SYNC) {
+                // keep the consumer warps within one tile of each other, so a stage is
+                // released (and refilled) as soon as the last of them has read it; every
+                // consumer warp reaches this barrier once per tile (its waits are bounded)
+                asm volatile("bar.sync 1, %0;" ::"r"(ROWS * 32) : "memory");
+                if (*abort_flag) ok = false;
+            }
             if (!ok) break;
-            if (y >= A.ny) continue;
-            collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
         }
     }
     __syncthreads();
