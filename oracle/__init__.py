@@ -30,6 +30,7 @@ listed in the design notes with its justification):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import math
 import os
@@ -50,16 +51,18 @@ _lib = None
 INNER_NODES = 6  # inner Gauss-Hermite rule for a_eq integrals (exact to degree 11)
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (plain C99, -O2, no vendor code)."""
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile liboracle.so with gcc (plain C99, -O2, no vendor code).  plant = k > 0 (tests
+    only) builds the variant with mistake k planted (see lb_oracle.c)."""
     os.makedirs(_BUILD, exist_ok=True)
+    path = _LIB_PATH if plant == 0 else os.path.join(_BUILD, f"liboracle_plant{plant}.so")
     newest = max(os.path.getmtime(s) for s in _SOURCES)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=gnu99", "-shared", "-fPIC", "-o", tmp, *_SOURCES, "-lm"]
+    if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+        tmp = path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu99", "-shared", "-fPIC", f"-DORACLE_PLANT={plant}", "-o", tmp, *_SOURCES, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 class _Params(ctypes.Structure):
@@ -74,26 +77,41 @@ class _Params(ctypes.Structure):
     ]
 
 
+def _bind(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(_Params)
+    lib.oracle_lb_run.argtypes = [pp, dp, ctypes.c_int, dp]
+    lib.oracle_lb_run_from.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
+    lib.oracle_lb_moments.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp, dp, dp]
+    lib.oracle_feq.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    lib.oracle_force.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, dp]
+    lib.oracle_lb_init_shear.argtypes = [pp, ctypes.c_double, ctypes.c_double, dp]
+    lib.oracle_dvm_run.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, dp, dp, dp]
+    lib.oracle_dvm_dt.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double]
+    lib.oracle_dvm_dt.restype = ctypes.c_double
+    return lib
+
+
+@contextlib.contextmanager
+def planted(k: int):
+    """Tests only: run the oracle with mistake k planted while the context is open."""
+    global _lib
+    _load()
+    old = _lib
+    _lib = _bind(ctypes.CDLL(build(plant=k)))
+    try:
+        yield
+    finally:
+        _lib = old
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            dp = ctypes.POINTER(ctypes.c_double)
-            pp = ctypes.POINTER(_Params)
-            lib.oracle_lb_run.argtypes = [pp, dp, ctypes.c_int, dp]
-            lib.oracle_lb_run_from.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, dp]
-            lib.oracle_lb_moments.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp, dp, dp]
-            lib.oracle_feq.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_double, dp]
-            lib.oracle_force.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, dp]
-            lib.oracle_lb_init_shear.argtypes = [pp, ctypes.c_double, ctypes.c_double, dp]
-            lib.oracle_dvm_run.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
-                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
-            lib.oracle_dvm_dt.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double]
-            lib.oracle_dvm_dt.restype = ctypes.c_double
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 

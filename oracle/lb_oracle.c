@@ -38,6 +38,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Test builds only: ORACLE_PLANT = k compiles mistake k into the stepper, so that the
+ * tests can check that the pins catch it (tests/test_oracle_planted.py).  0: none. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+#define PLANTED(k) (ORACLE_PLANT == (k))
+
 #define ORACLE_MAXQ 128
 #define ORACLE_MAXN 4
 #define ORACLE_MAXINNER 32
@@ -99,6 +106,7 @@ void oracle_feq(const oracle_lb_params *p, double rho, double ux, double uy, dou
     for (int a = 0; a < p->Q; ++a) feq[a] = 0.0;
     for (int n = 0; n <= p->N; ++n) {
         double inv_nfact = 1.0 / factorial(n);
+        if (PLANTED(5) && n == p->N) break; /* planted: highest Hermite order dropped */
         for (int t = 0; t < (1 << n); ++t) { /* index tuple: bit b set -> index b is y */
             int ky = __builtin_popcount((unsigned)t), kx = n - ky;
             double an = a_eq_component(p, rho, ux, uy, Teq, kx, ky);
@@ -127,7 +135,7 @@ void oracle_force(const oracle_lb_params *p, double rho, double ux, double uy, d
             double am1 = a_eq_component(p, rho, ux, uy, Teq, kx, ky - 1); /* a^(n-1) over i2..in */
             for (int a = 0; a < p->Q; ++a) {
                 double chi = hermite_he(kx, p->xi[2 * a]) * hermite_he(ky, p->xi[2 * a + 1]);
-                F[a] += inv * gy * am1 * chi;
+                F[a] += (PLANTED(1) ? -inv : inv) * gy * am1 * chi; /* planted 1: sign */
             }
         }
     }
@@ -184,7 +192,7 @@ static void collide_and_observe(const oracle_lb_params *p, const double *f, doub
             double gy = force_at(p, x, t);
             if (gy != 0.0) {
                 /* rho u = sum xi f~ + rho g dt/2; T of f: T(f~) + dt^2 g^2 / 8 */
-                uy += 0.5 * p->dt * gy;
+                if (!PLANTED(2)) uy += 0.5 * p->dt * gy; /* planted 2: no dt/2 correction */
                 T += p->dt * p->dt * gy * gy / 8.0;
                 oracle_force(p, rho, ux, uy, T, gy, F);
             } else {
@@ -197,9 +205,11 @@ static void collide_and_observe(const oracle_lb_params *p, const double *f, doub
                 sxy += p->xi[2 * a] * p->xi[2 * a + 1] * (fa - feq[a] + 0.5 * p->dt * F[a]);
                 double d = fa - p->w[a] * p->rho0;
                 h += d * d / p->w[a];
-                if (fstar) fstar[(size_t)a * plane + c] = fa - omega * (fa - feq[a]) + omega * tau * F[a];
+                if (fstar)
+                    fstar[(size_t)a * plane + c] =
+                        fa - omega * (fa - feq[a]) + omega * (PLANTED(3) ? 1.0 : tau) * F[a]; /* planted 3 */
             }
-            sxy *= (1.0 - 0.5 * omega);
+            if (!PLANTED(6)) sxy *= (1.0 - 0.5 * omega); /* planted 6: no (1 - omega/2) */
             double xi_pos = 2.0 * pi * (double)x / (double)nx; /* x_i = i dx, dx = 2 pi / nx */
             mass += rho;
             mx += rho * ux;
@@ -234,7 +244,8 @@ static void lax_wendroff_line(const double *in, double *out, int n, size_t s, do
         double fm = in[(size_t)((i - 1 + n) % n) * s];
         double f0 = in[(size_t)i * s];
         double fp = in[(size_t)((i + 1) % n) * s];
-        out[(size_t)i * s] = f0 - 0.5 * C * (fp - fm) + 0.5 * C * C * (fp - 2.0 * f0 + fm);
+        double Cs = PLANTED(4) ? -C : C; /* planted 4: streaming against xi */
+        out[(size_t)i * s] = f0 - 0.5 * Cs * (fp - fm) + 0.5 * Cs * Cs * (fp - 2.0 * f0 + fm);
     }
 }
 
