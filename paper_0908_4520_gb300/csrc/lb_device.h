@@ -25,6 +25,7 @@ struct Tab {
     R a[kMaxNA];              // axis node values (xi components)
     R a2[kMaxNA];             // a_i^2
     R wm[kMaxNA];             // 1-D marginal weights W_i (product-weight sets: w_a = W[ix] W[iy])
+    R wminv[kMaxNA];          // 1 / W_i
     R hn[kMaxNA][kMaxN + 1];  // He_k(a_i) / k!
     R whn[kMaxNA][kMaxN + 1]; // W_i He_k(a_i) / k!
     R lw[kMaxNA][3];          // Lax-Wendroff weights of f*(x-1), f*(x), f*(x+1)

@@ -60,6 +60,7 @@ void build_tab(const VelocitySetInfo& vs, double dt, double dx, double scale, lb
         t.a[i] = (R)vs.axis[i];
         t.a2[i] = (R)(vs.axis[i] * vs.axis[i]);
         t.wm[i] = (R)wm[i];
+        t.wminv[i] = (R)(1.0 / wm[i]);
         double fact = 1.0;
         for (int k = 0; k <= lbk::kMaxN; ++k) {
             if (k > 1) fact *= k;

@@ -390,6 +390,12 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_TILE_SYNC
 #define LB_TMA_TILE_SYNC -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
 #endif
+#ifndef LB_TMA_EVICT_LAST
+#define LB_TMA_EVICT_LAST 0
+#endif
+#ifndef LB_PAIR_COLLISION
+#define LB_PAIR_COLLISION 1  // one cell per lane: collide velocity pairs as packed f32x2 values
+#endif
 #ifndef LB_TMA_HALO
 #define LB_TMA_HALO -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
 #endif
@@ -759,6 +765,151 @@ __device__ __forceinline__ R force_at_level(const Args<R>& A, long long lvl) {
     return A.force_amp != 0.0 ? (R)(A.force_amp * cos(A.force_freq * (double)lvl * A.dt)) : R(0);
 }
 
+// The same collision with one cell per lane and the velocities taken in pairs (a, a + 1)
+// of equal x node (a = ix NA + iy, iy even), each pair one packed f32x2 value: the
+// per-velocity work (moment sums, diagnostics, equilibrium, relaxation) runs at half the
+// instruction count.  Product-weight Gauss-Hermite sets (NA even), FP32 arithmetic.
+// Moments as in collide_cell, with the y-node sums kept as pairs and the x-node sums
+// reduced when the x node changes; H = sum_ix (1/W_ix) sum_iy d^2 / W_iy.
+template <class VS>
+struct PairCollision {
+    static constexpr bool value = VS::kProductWeights && !VS::kOnLattice && VS::NA % 2 == 0;
+};
+
+template <class VS, int N, bool COLLIDE, class F>
+__device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t, float rho0, float omega,
+                                                             float sigma_fac, int isothermal, bool diag,
+                                                             bool forced, float gf, float tau, float dt, F&& fpair) {
+    using R = float;
+    constexpr int NA = VS::NA, NP = VS::Q / 2, NJ = NA / 2;
+    const f2 z2 = f2{0.f, 0.f};
+    f2 Ryp[NJ];
+    R C[NA];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) Ryp[j] = z2;
+    // x-node sums, one pair accumulator live at a time (the pairs come in x-node order)
+    static_for<0, NA>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        f2 cp = z2;
+        static_for<0, NJ>([&](auto jc) {
+            constexpr int J = decltype(jc)::value;
+            const f2 v = fpair(std::integral_constant<int, I * NJ + J>{});
+            cp = vadd(cp, v);
+            Ryp[J] = vadd(Ryp[J], v);
+        });
+        C[I] = cp.x + cp.y;
+    });
+    R drho = C[0], jx = t.a[0] * C[0];
+    R en = t.a2[0] * C[0];
+#pragma unroll
+    for (int i = 1; i < NA; ++i) {
+        drho += C[i];
+        jx = fmaf(t.a[i], C[i], jx);
+        en = fmaf(t.a2[i], C[i], en);
+    }
+    f2 jyp = z2, eyp = z2;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        jyp = vfma(f2{t.a[2 * j], t.a[2 * j + 1]}, Ryp[j], jyp);
+        eyp = vfma(f2{t.a2[2 * j], t.a2[2 * j + 1]}, Ryp[j], eyp);
+    }
+    R jy = jyp.x + jyp.y;
+    en += eyp.x + eyp.y;
+    CellOut<R> o;
+    R pxy = 0.f, h = 0.f;
+    if (diag) {
+        static_for<0, NA>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            f2 pp = z2, hp = z2;
+            static_for<0, NJ>([&](auto jc) {
+                constexpr int J = decltype(jc)::value;
+                const f2 v = fpair(std::integral_constant<int, I * NJ + J>{});
+                pp = vfma(f2{t.a[2 * J], t.a[2 * J + 1]}, v, pp);
+                hp = vfma(vmul(v, f2{t.wminv[2 * J], t.wminv[2 * J + 1]}), v, hp);
+            });
+            pxy = fmaf(t.a[I], pp.x + pp.y, pxy);
+            h = fmaf(t.wminv[I], hp.x + hp.y, h);
+        });
+    }
+    const R rho = rho0 + drho;
+    const R rg = forced ? __fmul_rn(rho, gf) : 0.f;
+    if (forced) jy = fmaf(0.5f * dt, rg, jy);
+    const R inv = 1.0f / rho;
+    const R ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
+    const R u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
+    R th = 0.f;
+    if (!isothermal) {
+        R e2 = __fsub_rn(__fsub_rn(en, __fadd_rn(drho, drho)), __fmul_rn(rho, u2));
+        if (forced) e2 = fmaf(__fmul_rn(dt, rg), uy, e2);
+        th = __fmul_rn(__fmul_rn(e2, 0.5f), inv);
+    }
+    o.drho = drho;
+    o.jx = jx;
+    o.jy = jy;
+    o.ux = ux;
+    o.uy = uy;
+    o.th = th;
+    R pneq = __fsub_rn(pxy, __fmul_rn(rho, __fmul_rn(ux, uy)));
+    if (forced) pneq = fmaf(__fmul_rn(0.5f * dt, rg), ux, pneq);
+    o.sig = __fmul_rn(sigma_fac, pneq);
+    o.h = h;
+    if constexpr (COLLIDE) {
+        R cx[N + 1], cy[N + 1];
+        cx[0] = cy[0] = 1.f;
+        cx[1] = ux;
+        cy[1] = uy;
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+            const R kth = __fmul_rn((R)k, th);
+            cx[k + 1] = fmaf(ux, cx[k], __fmul_rn(kth, cx[k - 1]));
+            cy[k + 1] = fmaf(uy, cy[k], __fmul_rn(kth, cy[k - 1]));
+        }
+        if (forced) {
+            const R tg = __fmul_rn(tau, gf);
+#pragma unroll
+            for (int k = N; k >= 1; --k) cy[k] = fmaf(__fmul_rn((R)k, tg), cy[k - 1], cy[k]);
+        }
+        // y factors of the y-node pairs: QY[j][ky] = W_j He_ky(a_j)/ky! c_ky(u_y)
+        f2 QYp[NJ][N + 1];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            QYp[j][0] = f2{t.wm[2 * j], t.wm[2 * j + 1]};
+#pragma unroll
+            for (int ky = 1; ky <= N; ++ky)
+                QYp[j][ky] = vmul(f2{t.whn[2 * j][ky], t.whn[2 * j + 1][ky]}, vsplat<f2>(cy[ky]));
+        }
+        const f2 om1 = vsplat<f2>(1.f - omega);
+        static_for<0, NA>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            R PX[N + 1];
+            {
+                R px[N + 1];
+#pragma unroll
+                for (int ky = 0; ky <= N; ++ky) {
+                    R sacc = ky == 0 ? 0.f : 1.f;
+#pragma unroll
+                    for (int kx = 1; kx <= N - ky; ++kx) sacc = fmaf(cx[kx], t.hn[I][kx], sacc);
+                    px[ky] = sacc;
+                }
+                const R ow = omega * t.wm[I];
+                PX[0] = __fmul_rn(ow, fmaf(rho, px[0], drho));
+                const R owr = __fmul_rn(ow, rho);
+#pragma unroll
+                for (int ky = 1; ky <= N; ++ky) PX[ky] = __fmul_rn(owr, px[ky]);
+            }
+            static_for<0, NJ>([&](auto jc) {
+                constexpr int J = decltype(jc)::value;
+                f2 od = vmul(vsplat<f2>(PX[0]), QYp[J][0]);
+#pragma unroll
+                for (int ky = 1; ky <= N; ++ky) od = vfma(vsplat<f2>(PX[ky]), QYp[J][ky], od);
+                f2& fa = fpair(std::integral_constant<int, I * NJ + J>{});
+                fa = vfma(fa, om1, od);
+            });
+        });
+    }
+    return o;
+}
+
 // Collision and store (or the moment outputs) of the V cells (g.x .., y) whose
 // streamed populations are in ft.  Diagnostics are reduced over the warp in
 // FP32 and added to acc (lane 0) in FP64.
@@ -782,9 +933,29 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             gf = gl[0];
         }
     }
-    const CellOut<T> co = collide_cell<VS, N, R, T, STEP>(
-        A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
-        (R)A.dt, [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
+    CellOut<T> co;
+    if constexpr (V == 1 && std::is_same<R, float>::value && PairCollision<VS>::value &&
+                  LB_PAIR_COLLISION) {
+        // one cell per lane: velocity pairs as packed f32x2 values
+        constexpr int NP = Q / 2;
+        f2 fp[NP];
+        static_for<0, NP>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            fp[m] = f2{ft[2 * m], ft[2 * m + 1]};
+        });
+        co = collide_cell_pairs<VS, N, STEP>(
+            A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
+            (R)A.dt, [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
+        static_for<0, NP>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            ft[2 * m] = fp[m].x;
+            ft[2 * m + 1] = fp[m].y;
+        });
+    } else {
+        co = collide_cell<VS, N, R, T, STEP>(
+            A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
+            (R)A.dt, [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
+    }
     if constexpr (KIND == kMoments) {
         if (g.own) {
             static_for<0, V>([&](auto kc) {
@@ -1103,11 +1274,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
+    if constexpr (LB_TMA_EVICT_LAST) {
+        // the halo rows and columns of a box are read again by the neighbouring tiles:
+        // ask L2 to keep the lines (evict-last) so those re-reads do not go to DRAM
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "l"(pol)
+            : "memory");
+    } else {
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+            "[%2];" ::"r"(smem_u32(dst)),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+            : "memory");
+    }
 }
 
 template <class VS, int N, class S>
