@@ -106,6 +106,11 @@ typedef struct {
      * plain-load kernel (step_kernel 2 is LB_ERR_UNSUPPORTED).  0 (default): free wave. */
     double force_amp;
     double force_freq;
+    /* Test facility for the failure detection of the TMA-staged step kernel: 1 = its
+     * producer in block 0 withholds the first stage of its first tile, so that block's
+     * bounded waits run out (about a second each) and the next synchronising call returns
+     * LB_ERR_TIMEOUT; the context stays usable.  0 (default) in normal use. */
+    int test_withhold_stage;
 } lb_params;
 
 /* One diagnostics record per time level n (t = n dt), FP64 sums over the grid:

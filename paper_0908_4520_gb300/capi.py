@@ -42,6 +42,7 @@ class lb_params(ctypes.Structure):
         ("storage_scale", ctypes.c_double), ("step_kernel", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
         ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double),
+        ("test_withhold_stage", ctypes.c_int),
     ]
 
 

@@ -184,6 +184,7 @@ struct lb_handle {
         A.dt = dt;
         A.force_amp = p.force_amp;
         A.force_freq = p.force_freq;
+        A.withhold_stage = p.test_withhold_stage;
         A.sinx = static_cast<const R*>(sin_d);
         A.cosx = static_cast<const R*>(cos_d);
         A.partials = partials;
@@ -366,6 +367,7 @@ void lb_params_default(lb_params* p) {
     p->step_kernel = 0;
     p->force_amp = 0.0;
     p->force_freq = 0.0;
+    p->test_withhold_stage = 0;
 }
 
 const char* lb_status_string(lb_status s) {

@@ -109,9 +109,21 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
                     ft[a] = fma(lx0, gl, fma(lx1, g0, lx2 * gr));
                 });
             }
-            const CellOut<float> co = collide_cell<VS, N, float, float, true>(
+            // velocity pairs of equal x node as packed f32x2 values (the one-cell-per-lane
+            // collision of the single-lattice kernels)
+            f2 fp[Q / 2];
+            static_for<0, Q / 2>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                fp[m] = f2{ft[2 * m], ft[2 * m + 1]};
+            });
+            const CellOut<float> co = collide_cell_pairs<VS, N, true>(
                 t, 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
-                [&](auto ac) -> float& { return ft[decltype(ac)::value]; });
+                [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
+            static_for<0, Q / 2>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                ft[2 * m] = fp[m].x;
+                ft[2 * m + 1] = fp[m].y;
+            });
             uint32_t r = Is16<S>::value ? sr_seed(level, c) : 0u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {

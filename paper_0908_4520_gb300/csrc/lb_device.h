@@ -57,6 +57,7 @@ struct Args {
     int raw;                  // 1: src holds f~ itself (no streaming)
     int isothermal;
     int diag_every;           // record diagnostics when level % diag_every == 0
+    int withhold_stage;       // test of the bounded waits (lb_params.test_withhold_stage)
     R omega, rho0;
     R sigma_fac;              // 1 - omega / 2
     R tau;                    // collision time of Eq. bgk

@@ -22,7 +22,8 @@ class Lattice:
     def __init__(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, precision: str = "f32",
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
                  diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None,
-                 step_kernel: str = "auto", force_amp: float = 0.0, force_freq: float = 0.0):
+                 step_kernel: str = "auto", force_amp: float = 0.0, force_freq: float = 0.0,
+                 test_withhold_stage: int = 0):
         p = capi.lb_params_default()
         p.quadrature = capi.QUADRATURES[quadrature]
         p.n_eq, p.nx, p.ny, p.kn = n_eq, nx, ny, kn
@@ -35,6 +36,7 @@ class Lattice:
         p.stream = stream
         p.step_kernel = {"auto": 0, "plain": 1, "tma": 2}[step_kernel]
         p.force_amp, p.force_freq = force_amp, force_freq
+        p.test_withhold_stage = int(test_withhold_stage)
         self.quadrature, self.n_eq, self.nx, self.ny = quadrature, n_eq, nx, ny
         self.h = capi.lb_create_ex(p)
         inf = capi.lb_get_info(self.h)
