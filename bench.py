@@ -260,7 +260,7 @@ def run_gpu(args):
     # end-to-end through the C-ABI with host buffers: fields in, one record out per step, u_y back
     L = main_L
     e2e = None
-    if rank == 0 or world > 1:
+    if True:  # every rank: the job's end-to-end time is the slowest rank's
         x = 2 * np.pi * np.arange(nx) / nx
         y = 2 * np.pi * np.arange(ny) / ny
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -273,6 +273,8 @@ def run_gpu(args):
         dptr = lambda t: ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))
         e2e_steps = args.e2e_steps or args.steps
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         capi.check(capi.lib.lb_init_fields(L.h, dptr(rho_h), dptr(ux_h), dptr(uy_h), None), L.h)
         for _ in range(e2e_steps):
@@ -280,10 +282,10 @@ def run_gpu(args):
             capi.lb_diagnostics(L.h, 1)
         capi.check(capi.lib.lb_moments(L.h, None, None, dptr(out_h), None, None), L.h)
         t1 = time.perf_counter()
-        el = t1 - t0
-        h2d = 3 * 8 * ncell / e2e_steps
-        d2h = (64 * e2e_steps + 8 * ncell) / e2e_steps
-        e2e = {"value": ncell * e2e_steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+        el = reduce_max_ms((t1 - t0) * 1e3, dist, "cuda") / 1e3
+        h2d = world * 3 * 8 * ncell / e2e_steps  # all ranks' copies
+        d2h = world * (64 * e2e_steps + 8 * ncell) / e2e_steps
+        e2e = {"value": weak_value(ncell, world, e2e_steps, el * 1e3), "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
                "note": "timed: one solve through the C-ABI: lb_init_fields from pinned host rho/ux/uy, then "
                        "the same number of levels as the device-timed run, each followed by a read of its "
