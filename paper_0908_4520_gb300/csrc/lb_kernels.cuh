@@ -388,7 +388,7 @@ struct Pack<float, 2> {
 #define LB_TMA_K 0
 #endif
 #ifndef LB_TMA_TILE_SYNC
-#define LB_TMA_TILE_SYNC -1  // -1: per set and storage (see TmaCfg), else the mode for all
+#define LB_TMA_TILE_SYNC -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
 #endif
 #ifndef LB_TMA_EVICT_LAST
 #define LB_TMA_EVICT_LAST 1  // TMA loads keep their lines in L2 for the neighbouring tiles (-3 % DRAM reads)
@@ -434,11 +434,8 @@ struct TmaCfg {
     // 16-bit 12.1 / 15.9 / 14.4; D2Q64 FP32 5.38 / 4.95 / 4.97; D2Q64 16-bit 4.37 / 6.40 / 6.28.
     static constexpr bool FP32_Q64 = sizeof(S) == 4 && VS::Q > 40;
     static constexpr bool HALO = LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64));
-    // 0: none; 1: bar.sync of the consumer warps after every tile; 2: the same bound on the
-    // drift (one tile) with an mbarrier per tile parity: arrive after tile t, wait for
-    // tile t - 1 to be finished by every consumer warp
-    static constexpr int TILE_SYNC =
-        LB_TMA_TILE_SYNC >= 0 ? LB_TMA_TILE_SYNC : ((HALO && sizeof(S) == 4 && VS::Q == 36) ? 1 : 0);
+    static constexpr bool TILE_SYNC =
+        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && HALO && sizeof(S) == 4 && VS::Q == 36);
     static constexpr int TWO = HALO ? 30 : TW;           // cells a tile row produces
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
     static constexpr int BW = HALO ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
@@ -1313,7 +1310,6 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
     uint64_t* const full = reinterpret_cast<uint64_t*>(smem_raw + NS * C::STAGE_BYTES);
     uint64_t* const empty = full + NS;
     __shared__ int s_abort;
-    __shared__ uint64_t tile_done[2];  // per tile parity: every consumer warp finished it
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
@@ -1321,8 +1317,6 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], ROWS);
         }
-        mbar_init(&tile_done[0], ROWS);
-        mbar_init(&tile_done[1], ROWS);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1379,7 +1373,6 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
         // stage index and parity advance with the stream of groups (NG per tile)
         int st_i = 0;
         uint32_t st_ph = 0;
-        uint32_t ti = 0;  // tiles finished by this warp
         for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
             const int ty = tile / A.ntiles_x;
             const int tx = tile - ty * A.ntiles_x;
@@ -1490,19 +1483,12 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             });
             if (ok && y < A.ny)
                 collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
-            if constexpr (C::TILE_SYNC == 1) {
+            if constexpr (C::TILE_SYNC) {
                 // keep the consumer warps within one tile of each other, so a stage is
                 // released (and refilled) as soon as the last of them has read it; every
                 // consumer warp reaches this barrier once per tile (its waits are bounded)
                 asm volatile("bar.sync 1, %0;" ::"r"(ROWS * 32) : "memory");
                 if (*abort_flag) ok = false;
-            } else if constexpr (C::TILE_SYNC == 2) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tile_done[ti & 1u]);
-                if (ti >= 1 && !mbar_wait(&tile_done[(ti - 1) & 1u], ((ti - 1) >> 1) & 1u, A.status))
-                    *abort_flag = 1;
-                if (*abort_flag) ok = false;
-                ++ti;
             }
             if (!ok) break;
         }
