@@ -399,6 +399,9 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_HALO
 #define LB_TMA_HALO -1  // -1: per set and storage (see TmaCfg), 0: never, 1: always
 #endif
+#ifndef LB_TMA_NS_TILES
+#define LB_TMA_NS_TILES 2  // ring depth cap, in tiles of stages
+#endif
 #ifndef LB_TMA_SMEM
 #define LB_TMA_SMEM (200 * 1024)
 #endif
@@ -448,7 +451,7 @@ struct TmaCfg {
     static constexpr int NG = (VS::Q + K - 1) / K;      // stages per tile
     static constexpr int STAGE_BYTES = (K * SLOT * (int)sizeof(S) + 127) / 128 * 128;
     static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
-    static constexpr int NS = NS_FIT < 2 * NG ? NS_FIT : 2 * NG;
+    static constexpr int NS = NS_FIT < LB_TMA_NS_TILES * NG ? NS_FIT : LB_TMA_NS_TILES * NG;
     static constexpr int THREADS = 32 * (ROWS + 1);     // + one producer warp
     // registers a thread may hold: each SM sub-partition's 16384 registers are shared by
     // ceil(warps / 4) warps of the block (255 for 8 warps, 168 for 9..12, 128 for 13..16)
