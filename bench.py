@@ -141,10 +141,12 @@ def ncu_traffic(quad):
 # ----------------------------------------------------------------------------- GPU arm
 
 def workload_name(args):
-    if args.n == 4096 and args.quad == "D2Q36-GH" and args.n_eq == 3 and args.precision == "f32":
+    if (args.n == 4096 and args.quad == "D2Q36-GH" and args.n_eq == 3 and args.precision == "f32"
+            and args.scheme == "second_order"):
         return WORKLOAD
+    scheme = ", first-order scheme (Eq. slb)" if args.scheme == "first_order" else ""
     return (f"standing shear wave {args.n}x{args.n}, {args.quad}, N={args.n_eq}, {args.precision} deviations, "
-            f"Kn={args.kn}")
+            f"Kn={args.kn}{scheme}")
 
 
 def kernel_label(args, tma):
@@ -180,9 +182,10 @@ def dvm_crosscheck(capi, Lattice, args, n=256, t_end=6.0):
             "lb": f"{args.quad} N={args.n_eq}, FP32"}
 
 
-def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32"):
+def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32",
+                    scheme="second_order"):
     stream = torch.cuda.Stream()
-    L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream)
+    L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream, scheme=scheme)
     L.init_shear_wave(1e-3, 1e-3)
     L.step(warmup)
     L.synchronize()
@@ -221,7 +224,7 @@ def run_gpu(args):
         if not quad:
             continue
         L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn,
-                                                  args.n_eq, args.precision)
+                                                  args.n_eq, args.precision, args.scheme)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -344,11 +347,11 @@ def run_gpu(args):
 
 # ----------------------------------------------------------------------------- oracle (CPU) legs
 
-def oracle_sample(quad, rows, steps, kn):
+def oracle_sample(quad, rows, steps, kn, n_eq=3, scheme="second_order"):
     import oracle
 
     oracle.build()
-    P = oracle.Problem(quad, 3, 4096, rows, kn)
+    P = oracle.Problem(quad, n_eq, 4096, rows, kn, scheme=scheme)
     f = P.init_shear(1e-3, 1e-3)
     t0 = time.perf_counter()
     P.run(f, steps, record=True)
@@ -357,9 +360,9 @@ def oracle_sample(quad, rows, steps, kn):
 
 
 def cpu_baseline(args):
-    mlups, el = oracle_sample(args.quad, args.cpu_rows, args.cpu_steps, args.kn)
+    mlups, el = oracle_sample(args.quad, args.cpu_rows, args.cpu_steps, args.kn, args.n_eq, args.scheme)
     return {"value": round(mlups, 5), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, {args.quad} N=3, periodic 4096x{args.cpu_rows} slab of the workload, "
+            "sample": f"FP64 oracle, {args.quad} N={args.n_eq}, periodic 4096x{args.cpu_rows} slab of the workload, "
                       f"{args.cpu_steps} steps with records ({el:.1f} s), single thread"}
 
 
@@ -698,6 +701,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--n-eq", type=int, default=3)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16", "bf16"])
+    ap.add_argument("--scheme", default="second_order", choices=["second_order", "first_order"])
     ap.add_argument("--kn", type=float, default=0.1)
     ap.add_argument("--e2e-steps", type=int, default=0, help="levels of the end-to-end leg (0: --steps)")
     ap.add_argument("--cpu-rows", type=int, default=48)

@@ -79,9 +79,23 @@ typedef enum { LB_F32 = 0, LB_F64 = 1, LB_BF16 = 2, LB_F16 = 3 } lb_precision;
  * PAPER:  kn is Eq. KN, tau = kn. */
 typedef enum { LB_KN_LAMBDA = 0, LB_KN_PAPER = 1 } lb_kn_convention;
 
+/* Time discretisation of the collision (Sec. 2.2).
+ * SECOND_ORDER (default): Eq. 2order; the state is f~, omega = dt / (tau + dt/2),
+ *   rho u = sum xi f~ + rho g dt/2 and sigma_xy carries the factor (1 - omega/2).
+ * FIRST_ORDER: the standard LB of Eq. slb (first-order upwind along the
+ *   characteristic); the state is f itself, omega = dt / tau (the relaxation time
+ *   tau/dt without the -1/2 correction), the force enters as dt g_alpha, and
+ *   rho u = sum xi f, sigma_xy = sum xi_x xi_y (f - f^eq).  It is linearly unstable
+ *   for omega >= 2, so lb_create_ex rejects tau <= dt/2 (LB_ERR_ARG).  Streaming is
+ *   the velocity set's own in both (exact shift, or Lax-Wendroff off-lattice). */
+typedef enum { LB_SCHEME_SECOND_ORDER = 0, LB_SCHEME_FIRST_ORDER = 1 } lb_scheme;
+
 typedef struct {
     lb_quadrature quadrature;
-    int n_eq;                  /* Hermite order N of the equilibrium, 2..4 */
+    int n_eq;                  /* Hermite order N of the equilibrium, 1..4.  N = 1 is the
+                                  first-order expansion f^eq = w rho (1 + xi.u) of Sec. 3.3
+                                  (Eq. lbm1, the isothermal linearised BGK form): T does not
+                                  enter it and is reported only */
     int nx, ny;                /* periodic grid; nx even, >= 2; ny >= 1 */
     double kn;                 /* Knudsen number (> 0), see kn_convention */
     lb_precision precision;    /* default LB_F32 */
@@ -111,12 +125,14 @@ typedef struct {
      * bounded waits run out (about a second each) and the next synchronising call returns
      * LB_ERR_TIMEOUT; the context stays usable.  0 (default) in normal use. */
     int test_withhold_stage;
+    lb_scheme scheme;          /* default LB_SCHEME_SECOND_ORDER */
 } lb_params;
 
 /* One diagnostics record per time level n (t = n dt), FP64 sums over the grid:
  * mass = sum rho, mom_x/mom_y = sum rho u, amp = 2/(nx ny) sum u_y sin(x_i),
  * shear = 2/(nx ny) sum sigma_xy cos(x_i) with sigma_xy = (1 - omega/2)
- * sum xi_x xi_y (f~ - f^eq) (pressure-tensor sign), hnorm = sum (f~ - w rho0)^2 / w,
+ * sum xi_x xi_y (f~ - f^eq) (pressure-tensor sign; factor 1 for LB_SCHEME_FIRST_ORDER),
+ * hnorm = sum (f~ - w rho0)^2 / w,
  * x_i = i dx.  flags != 0 marks a non-finite sum. */
 typedef struct {
     double t, mass, mom_x, mom_y, amp, shear, hnorm, flags;

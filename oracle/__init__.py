@@ -14,7 +14,8 @@ quadrature.py  velocity sets: Golub-Welsch Gauss-Hermite rules and products,
                matching.
 lb_oracle.c    plain FP64 LB stepper (moments, tensor-form Hermite
                equilibrium and body-force term of Sec. 2.1, Eq. 2order
-               collision, exact shift or Lax-Wendroff streaming, observables).
+               or Eq. slb collision, exact shift or Lax-Wendroff streaming,
+               observables).
 dvm_oracle.c   reduced linearised-BGK DVM of Sec. 3.3 (Eqs. ga, gb, unforced).
 linear.py      linear-mode matrix of the scheme and the continuous DVM
                dispersion relation (pins).
@@ -26,7 +27,8 @@ listed in the design notes with its justification):
 * Kn convention "lambda" (default): the mean free path lambda = mu/p
   sqrt(pi R T / 2), so the collision time of Eq. bgk is tau = Kn sqrt(2/pi);
   convention "paper": tau = Kn (Eq. KN).
-* omega = dt / (tau + dt/2) (Eq. 2order).
+* omega = dt / (tau + dt/2) (Eq. 2order); omega = dt / tau for the first-order
+  scheme of Eq. slb.
 """
 from __future__ import annotations
 
@@ -74,6 +76,7 @@ class _Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("isothermal", ctypes.c_int), ("ninner", ctypes.c_int),
         ("zin", ctypes.POINTER(ctypes.c_double)), ("win", ctypes.POINTER(ctypes.c_double)),
         ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double), ("force_uniform", ctypes.c_int),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -131,11 +134,15 @@ class Problem:
     """One standing-shear-wave configuration for the oracle.
 
     force_amp, force_freq: body force g = (0, g_y), g_y = force_amp sin(x_i) cos(force_freq t)
-    (force_uniform: g_y = force_amp cos(force_freq t)); force_amp = 0 is the free wave."""
+    (force_uniform: g_y = force_amp cos(force_freq t)); force_amp = 0 is the free wave.
+    N: Hermite order of the equilibrium, 1..4.
+    scheme: "second_order" (Eq. 2order) or "first_order" (the standard LB of Eq. slb,
+    omega = dt / tau, no dt/2 corrections of the moments, sigma_xy without 1 - omega/2)."""
 
     def __init__(self, set_name: str, N: int, nx: int, ny: int, kn: float,
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
-                 force_amp: float = 0.0, force_freq: float = 0.0, force_uniform: bool = False):
+                 force_amp: float = 0.0, force_freq: float = 0.0, force_uniform: bool = False,
+                 scheme: str = "second_order"):
         self.vs = quadrature.velocity_set(set_name)
         self.set_name, self.N, self.nx, self.ny, self.kn = set_name, N, nx, ny, kn
         self.isothermal = isothermal
@@ -146,7 +153,13 @@ class Problem:
         else:
             self.dt = cfl * self.dx / float(np.max(np.abs(self.vs.xi[:, 0])))
         self.tau = collision_time(kn, kn_convention)
-        self.omega = self.dt / (self.tau + 0.5 * self.dt)
+        if scheme not in ("second_order", "first_order"):
+            raise ValueError(scheme)
+        self.scheme = scheme
+        if scheme == "first_order":
+            self.omega = self.dt / self.tau  # Eq. slb
+        else:
+            self.omega = self.dt / (self.tau + 0.5 * self.dt)  # Eq. 2order
         self._xi = np.ascontiguousarray(self.vs.xi, dtype=np.float64)
         self._w = np.ascontiguousarray(self.vs.w, dtype=np.float64)
         self._e = (np.ascontiguousarray(self.vs.e, dtype=np.int32) if self.vs.on_lattice else None)
@@ -156,7 +169,7 @@ class Problem:
                           self._e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if self._e is not None else None,
                           self.dx, self.dt, self.tau, 1.0, int(isothermal), INNER_NODES,
                           _dp(self._z), _dp(self._wz), float(force_amp), float(force_freq),
-                          int(force_uniform))
+                          int(force_uniform), int(scheme == "first_order"))
 
     @property
     def Q(self):

@@ -28,6 +28,12 @@
  *               periodic shift by e_alpha (Sec. 2.3); off-lattice: Lax-Wendroff
  *               along x then along y (the scheme named in Sec. 3.3 and the
  *               caption of the D2Q400 figure), periodic.
+ * First-order scheme (scheme = 1, the standard LB of Eq. slb, Sec. 2.2): the state is
+ * f itself and one step is f(r + xi dt, t + dt) = f - (dt/tau)(f - f^eq) + dt g_alpha,
+ * i.e. the collide line above with omega = dt / tau (so omega tau = dt), moments
+ * rho u = sum xi f with no dt/2 term, T of f with no correction, and
+ * sigma_xy = sum xi_x xi_y (f - f^eq); streaming as above.
+ * Hermite order N = 1 (Sec. 3.3, Eq. lbm1) is the n <= 1 part of the same sums.
  * Observables at each time level n are taken from f~(n), before collision:
  *   mass = sum rho, mom = sum rho u, A = 2/(nx ny) sum u_y sin(x_i),
  *   S = 2/(nx ny) sum sigma_xy cos(x_i),
@@ -44,6 +50,7 @@
 #define ORACLE_PLANT 0
 #endif
 #define PLANTED(k) (ORACLE_PLANT == (k))
+/* planted 7: the first-order scheme relaxes with the second-order omega */
 
 #define ORACLE_MAXQ 128
 #define ORACLE_MAXN 4
@@ -64,7 +71,15 @@ typedef struct {
     double force_amp;    /* A_f of g_y = A_f s(x_i) cos(phi t); 0: unforced */
     double force_freq;   /* phi */
     int force_uniform;   /* 1: s(x) = 1, 0: s(x) = sin(x_i) */
+    int scheme;          /* 0: Eq. 2order, 1: Eq. slb (first order) */
 } oracle_lb_params;
+
+/* relaxation rate of the scheme */
+static double scheme_omega(const oracle_lb_params *p)
+{
+    if (p->scheme == 1) return PLANTED(7) ? p->dt / (p->tau + 0.5 * p->dt) : p->dt / p->tau;
+    return p->dt / (p->tau + 0.5 * p->dt);
+}
 
 /* probabilists' Hermite polynomial He_k(x) by its three-term recurrence */
 static double hermite_he(int k, double x)
@@ -191,9 +206,11 @@ static void collide_and_observe(const oracle_lb_params *p, const double *f, doub
             cell_moments(p, f + c, plane, &rho, &ux, &uy, &T);
             double gy = force_at(p, x, t);
             if (gy != 0.0) {
-                /* rho u = sum xi f~ + rho g dt/2; T of f: T(f~) + dt^2 g^2 / 8 */
-                if (!PLANTED(2)) uy += 0.5 * p->dt * gy; /* planted 2: no dt/2 correction */
-                T += p->dt * p->dt * gy * gy / 8.0;
+                /* Eq. 2order: rho u = sum xi f~ + rho g dt/2; T of f: T(f~) + dt^2 g^2 / 8 */
+                if (p->scheme == 0) {
+                    if (!PLANTED(2)) uy += 0.5 * p->dt * gy; /* planted 2: no dt/2 correction */
+                    T += p->dt * p->dt * gy * gy / 8.0;
+                }
                 oracle_force(p, rho, ux, uy, T, gy, F);
             } else {
                 for (int a = 0; a < Q; ++a) F[a] = 0.0;
@@ -202,14 +219,15 @@ static void collide_and_observe(const oracle_lb_params *p, const double *f, doub
             double sxy = 0, h = 0;
             for (int a = 0; a < Q; ++a) {
                 double fa = f[(size_t)a * plane + c];
-                sxy += p->xi[2 * a] * p->xi[2 * a + 1] * (fa - feq[a] + 0.5 * p->dt * F[a]);
+                double fneq = fa - feq[a] + (p->scheme == 0 ? 0.5 * p->dt * F[a] : 0.0);
+                sxy += p->xi[2 * a] * p->xi[2 * a + 1] * fneq;
                 double d = fa - p->w[a] * p->rho0;
                 h += d * d / p->w[a];
                 if (fstar)
                     fstar[(size_t)a * plane + c] =
                         fa - omega * (fa - feq[a]) + omega * (PLANTED(3) ? 1.0 : tau) * F[a]; /* planted 3 */
             }
-            if (!PLANTED(6)) sxy *= (1.0 - 0.5 * omega); /* planted 6: no (1 - omega/2) */
+            if (p->scheme == 0 && !PLANTED(6)) sxy *= (1.0 - 0.5 * omega); /* planted 6: no (1 - omega/2) */
             double xi_pos = 2.0 * pi * (double)x / (double)nx; /* x_i = i dx, dx = 2 pi / nx */
             mass += rho;
             mx += rho * ux;
@@ -308,7 +326,7 @@ int oracle_lb_run_from(const oracle_lb_params *p, double *f, int n0, int nsteps,
         free(tmp);
         return -1;
     }
-    double omega = p->dt / (p->tau + 0.5 * p->dt);
+    double omega = scheme_omega(p);
     for (int s = 0; s < nsteps; ++s) {
         double *rec = diag ? diag + (size_t)s * 8 : NULL;
         double t = (double)(n0 + s) * p->dt;
@@ -337,7 +355,7 @@ int oracle_lb_moments(const oracle_lb_params *p, const double *f, int n, double 
                       double *uy, double *T, double *sxy)
 {
     if (!p || !f) return -1;
-    double omega = p->dt / (p->tau + 0.5 * p->dt);
+    double omega = scheme_omega(p);
     collide_and_observe(p, f, NULL, omega, (double)n * p->dt, NULL, rho, ux, uy, T, sxy);
     return 0;
 }

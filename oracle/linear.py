@@ -52,8 +52,9 @@ def lb_mode_matrix(xi, w, omega, dx, dt, k=1.0, e=None, isothermal=False):
     return S[:, None] * ((1.0 - omega) * np.eye(Q) + omega * P)
 
 
-def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False):
-    """A(n) and S(n), n = 0..nsteps, of the linearised scheme from u_y = u0 sin x."""
+def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False, scheme="second_order"):
+    """A(n) and S(n), n = 0..nsteps, of the linearised scheme from u_y = u0 sin x.
+    scheme "first_order" (Eq. slb) reads sigma_xy without the factor 1 - omega/2."""
     xi = np.asarray(xi, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
@@ -71,7 +72,7 @@ def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False
     S = np.empty(nsteps + 1)
     for n in range(nsteps + 1):
         c = np.sum(xi[:, 1] * f)
-        s = (1.0 - 0.5 * omega) * np.sum(kxy * (f - Pm @ f))
+        s = (1.0 - 0.5 * omega if scheme == "second_order" else 1.0) * np.sum(kxy * (f - Pm @ f))
         A[n] = -2.0 * c.imag
         S[n] = 2.0 * s.real
         f = M @ f
@@ -126,9 +127,11 @@ def _projection(xi, w, isothermal):
     return w[:, None] * Pm
 
 
-def lb_linear_forced_history(xi, w, omega, dx, dt, force_amp, phi, nsteps, e=None, isothermal=False):
+def lb_linear_forced_history(xi, w, omega, dx, dt, force_amp, phi, nsteps, e=None, isothermal=False,
+                             scheme="second_order"):
     """A(n), n = 0..nsteps, of the linearised scheme started at rest and driven by
-    g_y = force_amp sin(x_i) cos(phi t)."""
+    g_y = force_amp sin(x_i) cos(phi t).  For the first-order scheme of Eq. slb the
+    source is dt w_a xi_ay g as well (omega tau = dt) and u_y = sum xi_y f."""
     xi = np.asarray(xi, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
@@ -142,7 +145,8 @@ def lb_linear_forced_history(xi, w, omega, dx, dt, force_amp, phi, nsteps, e=Non
     A = np.empty(nsteps + 1)
     for n in range(nsteps + 1):
         g = force_amp * np.cos(phi * n * dt) / 2j  # e^{ix} coefficient of g_y
-        A[n] = -2.0 * (np.sum(xi[:, 1] * f) + 0.5 * dt * g).imag
+        shift = 0.5 * dt * g if scheme == "second_order" else 0.0
+        A[n] = -2.0 * (np.sum(xi[:, 1] * f) + shift).imag
         f = M @ f + S * (dt * w * xi[:, 1] * g)
     return A
 

@@ -184,8 +184,10 @@ struct lb_handle {
         const double om = std::is_same<R, float>::value ? lbh::snap_unit(omega) : omega;
         A.omega = (R)om;
         A.rho0 = (R)1.0;
-        A.sigma_fac = (R)(1.0 - 0.5 * om);
+        const bool first = p.scheme == LB_SCHEME_FIRST_ORDER;
+        A.sigma_fac = (R)(first ? 1.0 : 1.0 - 0.5 * om);
         A.tau = (R)tau;
+        A.hdt = (R)(first ? 0.0 : 0.5 * dt);
         A.dt = dt;
         A.force_amp = p.force_amp;
         A.force_freq = p.force_freq;
@@ -373,6 +375,7 @@ void lb_params_default(lb_params* p) {
     p->force_amp = 0.0;
     p->force_freq = 0.0;
     p->test_withhold_stage = 0;
+    p->scheme = LB_SCHEME_SECOND_ORDER;
 }
 
 const char* lb_status_string(lb_status s) {
@@ -437,7 +440,9 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     if (P.nx < 2 || (P.nx & 1)) return reject(LB_ERR_ARG, "nx must be even and >= 2");
     if (P.ny < 1) return reject(LB_ERR_ARG, "ny must be >= 1");
     if ((long long)P.nx * P.ny > (1LL << 31) - 1) return reject(LB_ERR_ARG, "grid too large");
-    if (P.n_eq < 2 || P.n_eq > 4) return reject(LB_ERR_ARG, "n_eq must be 2, 3 or 4");
+    if (P.n_eq < 1 || P.n_eq > 4) return reject(LB_ERR_ARG, "n_eq must be 1, 2, 3 or 4");
+    if (P.scheme != LB_SCHEME_SECOND_ORDER && P.scheme != LB_SCHEME_FIRST_ORDER)
+        return reject(LB_ERR_ARG, "unknown scheme");
     if (!(P.kn > 0) || !std::isfinite(P.kn)) return reject(LB_ERR_ARG, "kn must be positive");
     if (!(P.cfl > 0 && P.cfl <= 1.0)) return reject(LB_ERR_ARG, "cfl must be in (0, 1]");
     if (P.diag_capacity < 1) return reject(LB_ERR_ARG, "diag_capacity must be >= 1");
@@ -472,7 +477,16 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     for (double a : h->vs.axis) amax = std::max(amax, std::fabs(a));
     h->dt = h->vs.on_lattice ? h->dx / h->vs.c : P.cfl * h->dx / amax;
     h->tau = (P.kn_convention == LB_KN_LAMBDA) ? P.kn * std::sqrt(2.0 / M_PI) : P.kn;
-    h->omega = h->dt / (h->tau + 0.5 * h->dt);
+    if (P.scheme == LB_SCHEME_FIRST_ORDER) {
+        // Eq. slb: omega = dt / tau, linearly unstable for omega >= 2
+        if (!(h->tau > 0.5 * h->dt)) {
+            delete h;
+            return reject(LB_ERR_ARG, "the first-order scheme needs tau > dt/2 (omega = dt/tau < 2)");
+        }
+        h->omega = h->dt / h->tau;
+    } else {
+        h->omega = h->dt / (h->tau + 0.5 * h->dt);
+    }
     {
         lbk::Launch L{};
         L.kind = lbk::kQueryShape;

@@ -59,8 +59,9 @@ struct Args {
     int diag_every;           // record diagnostics when level % diag_every == 0
     int withhold_stage;       // test of the bounded waits (lb_params.test_withhold_stage)
     R omega, rho0;
-    R sigma_fac;              // 1 - omega / 2
+    R sigma_fac;              // 1 - omega / 2 (Eq. 2order), 1 (Eq. slb)
     R tau;                    // collision time of Eq. bgk
+    R hdt;                    // dt / 2 of the force corrections of the moments (Eq. 2order), 0 (Eq. slb)
     double dt;
     double force_amp;         // body force g_y = force_amp sin(x_i) cos(force_freq t); 0: none
     double force_freq;
@@ -96,7 +97,7 @@ struct Shape {
 
 struct Launch {
     int kind;                 // Kind
-    int n_eq;                 // 2..4
+    int n_eq;                 // 1..4
     int grid;                 // blocks (persistent grid-stride over tiles)
     cudaStream_t stream;
     const void* args;         // Args<float>/Args<double> matching the unit, or Shape* for kQueryShape

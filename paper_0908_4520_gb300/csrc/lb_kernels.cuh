@@ -624,14 +624,18 @@ struct CellOut {
 //    weights w_a = W_ix W_iy the weights fold into the per-axis factors, so
 //    omega (f^eq_a - w_a rho0) = sum_{ky<=N} PX[ix][ky] QY[iy][ky]
 //  * relaxation (Eq. 2order): f* = (1 - omega) f~ + omega f^eq, one FMA a velocity
-//  * body force g = (0, g) (Secs. 2.1, 2.2; forced): rho u_y = sum xi_y f~ + rho g dt/2,
-//    2 rho T gains dt rho g u_y, sigma_xy gains (dt/2) rho g u_x (the xy moment of
-//    the force term), and the force term relaxed with weight omega tau,
+//  * N = 1 (Sec. 3.3, Eq. lbm1): f^eq = w rho (1 + xi.u) has no xy moment, so
+//    sigma_xy = (1 - omega/2) Pi_xy, and neither has its force term w rho g xi_y
+//  * body force g = (0, g) (Secs. 2.1, 2.2; forced): rho u_y = sum xi_y f~ + rho g hdt,
+//    2 rho T gains 2 hdt rho g u_y, sigma_xy gains hdt rho g u_x (the xy moment of
+//    the force term), hdt = dt/2 (Eq. 2order; 0 for the first-order scheme of
+//    Eq. slb, whose stored variable is f itself), and the force term relaxed with
+//    weight omega tau (= dt for Eq. slb, where omega = dt / tau),
 //    omega tau g_a = omega w_a rho g sum_{ky>=1} c_kx c_{ky-1} He_kx He_ky / (kx! (ky-1)!),
 //    folds into the y factors: c_ky -> c_ky + ky tau g c_{ky-1} (ky >= 1)
 template <class VS, int N, class R, class T, bool COLLIDE, class F>
 __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R omega, R sigma_fac, int isothermal,
-                                                   bool diag, bool forced, T gf, R tau, R dt, F&& f) {
+                                                   bool diag, bool forced, T gf, R tau, R hdt, F&& f) {
     constexpr int NA = VS::NA;
     const T zero = vsplat<T>(R(0));
     T C[NA], Ry[NA];
@@ -669,14 +673,14 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
     }
     const T rho = vadd(vsplat<T>(rho0), drho);
     const T rg = forced ? vmul(rho, gf) : zero;  // rho g
-    if (forced) jy = vfma(vsplat<T>(R(0.5) * dt), rg, jy);
+    if (forced) jy = vfma(vsplat<T>(hdt), rg, jy);
     const T inv = vrcp(rho);
     const T ux = vmul(jx, inv), uy = vmul(jy, inv);
     const T u2 = vfma(ux, ux, vmul(uy, uy));
     T th = zero;
     if (!isothermal) {
         T e2 = vsub(vsub(en, vadd(drho, drho)), vmul(rho, u2));
-        if (forced) e2 = vfma(vmul(vsplat<T>(dt), rg), uy, e2);
+        if (forced) e2 = vfma(vmul(vsplat<T>(hdt + hdt), rg), uy, e2);
         th = vmul(vmul(e2, vsplat<T>(R(0.5))), inv);
     }
     o.drho = drho;
@@ -685,8 +689,11 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
     o.ux = ux;
     o.uy = uy;
     o.th = th;
-    T pneq = vsub(pxy, vmul(rho, vmul(ux, uy)));
-    if (forced) pneq = vfma(vmul(vsplat<T>(R(0.5) * dt), rg), ux, pneq);
+    T pneq = pxy;
+    if constexpr (N >= 2) {
+        pneq = vsub(pxy, vmul(rho, vmul(ux, uy)));
+        if (forced) pneq = vfma(vmul(vsplat<T>(hdt), rg), ux, pneq);
+    }
     o.sig = vmul(vsplat<T>(sigma_fac), pneq);
     o.h = h;
     if constexpr (COLLIDE) {
@@ -783,7 +790,7 @@ struct PairCollision {
 template <class VS, int N, bool COLLIDE, class F>
 __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t, float rho0, float omega,
                                                              float sigma_fac, int isothermal, bool diag,
-                                                             bool forced, float gf, float tau, float dt, F&& fpair) {
+                                                             bool forced, float gf, float tau, float hdt, F&& fpair) {
     using R = float;
     constexpr int NA = VS::NA, NP = VS::Q / 2, NJ = NA / 2;
     const f2 z2 = f2{0.f, 0.f};
@@ -837,14 +844,14 @@ __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t
     }
     const R rho = rho0 + drho;
     const R rg = forced ? __fmul_rn(rho, gf) : 0.f;
-    if (forced) jy = fmaf(0.5f * dt, rg, jy);
+    if (forced) jy = fmaf(hdt, rg, jy);
     const R inv = 1.0f / rho;
     const R ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
     const R u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
     R th = 0.f;
     if (!isothermal) {
         R e2 = __fsub_rn(__fsub_rn(en, __fadd_rn(drho, drho)), __fmul_rn(rho, u2));
-        if (forced) e2 = fmaf(__fmul_rn(dt, rg), uy, e2);
+        if (forced) e2 = fmaf(__fmul_rn(hdt + hdt, rg), uy, e2);
         th = __fmul_rn(__fmul_rn(e2, 0.5f), inv);
     }
     o.drho = drho;
@@ -853,8 +860,11 @@ __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t
     o.ux = ux;
     o.uy = uy;
     o.th = th;
-    R pneq = __fsub_rn(pxy, __fmul_rn(rho, __fmul_rn(ux, uy)));
-    if (forced) pneq = fmaf(__fmul_rn(0.5f * dt, rg), ux, pneq);
+    R pneq = pxy;
+    if constexpr (N >= 2) {
+        pneq = __fsub_rn(pxy, __fmul_rn(rho, __fmul_rn(ux, uy)));
+        if (forced) pneq = fmaf(__fmul_rn(hdt, rg), ux, pneq);
+    }
     o.sig = __fmul_rn(sigma_fac, pneq);
     o.h = h;
     if constexpr (COLLIDE) {
@@ -949,7 +959,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
         });
         co = collide_cell_pairs<VS, N, STEP>(
             A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
-            (R)A.dt, [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
+            A.hdt, [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
         static_for<0, NP>([&](auto mc) {
             constexpr int m = decltype(mc)::value;
             ft[2 * m] = fp[m].x;
@@ -958,7 +968,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     } else {
         co = collide_cell<VS, N, R, T, STEP>(
             A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
-            (R)A.dt, [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
+            A.hdt, [&](auto ac) -> T& { return ft[decltype(ac)::value]; });
     }
     if constexpr (KIND == kMoments) {
         if (g.own) {
@@ -1594,6 +1604,7 @@ cudaError_t launch_typed(const Launch& L) {
 template <class VS, class S, class R>
 cudaError_t launch_order(const Launch& L) {
     switch (L.n_eq) {
+        case 1: return launch_typed<VS, 1, S, R>(L);
         case 2: return launch_typed<VS, 2, S, R>(L);
         case 3: return launch_typed<VS, 3, S, R>(L);
         case 4: return launch_typed<VS, 4, S, R>(L);

@@ -17,13 +17,16 @@ class Lattice:
     step_kernel: "auto", "plain" (coalesced loads) or "tma" (TMA-staged); same results.
     force_amp, force_freq: body force g_y = force_amp sin(x_i) cos(force_freq t) driving the
     standing shear wave (0: free decay).
+    n_eq: Hermite order N of the equilibrium, 1..4 (1: f^eq = w rho (1 + xi.u)).
+    scheme: "second_order" (Eq. 2order, default) or "first_order" (the standard LB of
+    Eq. slb: omega = dt / tau, state f, no dt/2 corrections).
     """
 
     def __init__(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, precision: str = "f32",
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
                  diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None,
                  step_kernel: str = "auto", force_amp: float = 0.0, force_freq: float = 0.0,
-                 test_withhold_stage: int = 0):
+                 test_withhold_stage: int = 0, scheme: str = "second_order"):
         p = capi.lb_params_default()
         p.quadrature = capi.QUADRATURES[quadrature]
         p.n_eq, p.nx, p.ny, p.kn = n_eq, nx, ny, kn
@@ -37,6 +40,7 @@ class Lattice:
         p.step_kernel = {"auto": 0, "plain": 1, "tma": 2}[step_kernel]
         p.force_amp, p.force_freq = force_amp, force_freq
         p.test_withhold_stage = int(test_withhold_stage)
+        p.scheme = capi.SCHEMES[scheme]
         self.quadrature, self.n_eq, self.nx, self.ny = quadrature, n_eq, nx, ny
         self.h = capi.lb_create_ex(p)
         inf = capi.lb_get_info(self.h)

@@ -4,7 +4,8 @@ while all of them hold for the oracle as it is.
 
 Planted mistakes: 1 sign of the force term; 2 no rho g dt/2 in the momentum; 3 force
 relaxed with omega instead of omega tau; 4 Lax-Wendroff streaming against xi; 5 the
-highest Hermite order dropped from the equilibrium; 6 sigma_xy without (1 - omega/2).
+highest Hermite order dropped from the equilibrium; 6 sigma_xy without (1 - omega/2);
+7 the first-order scheme of Eq. slb relaxing with the second-order omega.
 """
 import numpy as np
 import pytest
@@ -65,7 +66,23 @@ def _p_j3():
     return np.max(np.abs(d[:, 4] - A)) < 1e-5 * np.max(np.abs(A))
 
 
-PINS = {"P-c": _p_c, "P-e": _p_e, "P-j1": _p_j1, "P-j2": _p_j2, "P-j3": _p_j3}
+def _p_k1():
+    """N = 1 equilibrium is w rho (1 + xi.u) (Sec. 3.3, Eq. lbm1)."""
+    P = oracle.Problem("D2Q36-GH", 1, 8, 1, 0.1)
+    xi, w = P.vs.xi, P.vs.w
+    ref = w * 1.03 * (1.0 + 0.021 * xi[:, 0] - 0.017 * xi[:, 1])
+    return np.max(np.abs(P.feq(1.03, 0.021, -0.017, 1.01) - ref)) < 1e-15
+
+
+def _p_l1():
+    """Eq. slb decays with the viscosity tau - dt/2 (Sec. 2.2)."""
+    P = oracle.Problem("D2Q9", 2, 128, 1, 0.02, kn_convention="paper", scheme="first_order")
+    f = P.init_shear(1e-4)
+    d = P.run(f, int(30 / P.dt))
+    return abs(oracle.decay_fit(d[:, 0], d[:, 4], 1.0) / (P.tau - 0.5 * P.dt) - 1) < 1e-3
+
+
+PINS = {"P-c": _p_c, "P-e": _p_e, "P-j1": _p_j1, "P-j2": _p_j2, "P-j3": _p_j3, "P-k1": _p_k1, "P-l1": _p_l1}
 
 
 def test_all_pins_hold_for_the_oracle():
@@ -77,8 +94,9 @@ def test_all_pins_hold_for_the_oracle():
     (2, {"P-j2", "P-j3"}),
     (3, {"P-j2", "P-j3"}),
     (4, {"P-e"}),
-    (5, {"P-c"}),
+    (5, {"P-c", "P-k1"}),
     (6, {"P-e"}),
+    (7, {"P-l1"}),
 ])
 def test_planted_mistake_is_caught(plant, expect_failing):
     with oracle.planted(plant):
