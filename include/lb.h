@@ -299,6 +299,18 @@ const char *lb_batch_last_error(const lb_batch *b);
 lb_status lb_dvm_run(int n_inst, const double *tau, int n_nodes, int nx, double cfl, double u0,
                      int nsteps, double *amp, double *shear, void *stream);
 
+/* The same DVM driven by the body force of the standing shear wave (Sec. 4, Eq. force,
+ * turned so that the flow is along y): g(x, t) = force_amp sin(x_i) cos(force_freq t).
+ * The reduced function of Eq. ga stays zero, so the force term of Eq. gb is g:
+ *   dG/dt + xi_k dG/dx = (u - G)/tau + g.
+ * The relaxation half steps integrate relaxation and force exactly (u gains the time
+ * integral of g, G - u decays by exp(-dt / (2 tau))).  Arguments, results and errors as
+ * lb_dvm_run (LB_ERR_ARG also for a non-finite force_amp or force_freq); force_amp = 0
+ * is lb_dvm_run. */
+lb_status lb_dvm_run_forced(int n_inst, const double *tau, int n_nodes, int nx, double cfl, double u0,
+                            double force_amp, double force_freq, int nsteps, double *amp, double *shear,
+                            void *stream);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free solve of one small shear wave.  The paper has no
  * counterpart: this is an engineering entry point for callers that cannot

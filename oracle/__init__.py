@@ -16,7 +16,7 @@ lb_oracle.c    plain FP64 LB stepper (moments, tensor-form Hermite
                equilibrium and body-force term of Sec. 2.1, Eq. 2order
                or Eq. slb collision, exact shift or Lax-Wendroff streaming,
                observables).
-dvm_oracle.c   reduced linearised-BGK DVM of Sec. 3.3 (Eqs. ga, gb, unforced).
+dvm_oracle.c   reduced linearised-BGK DVM of Sec. 3.3 (Eqs. ga, gb), free or driven.
 linear.py      linear-mode matrix of the scheme and the continuous DVM
                dispersion relation (pins).
 
@@ -92,6 +92,9 @@ def _bind(lib):
     lib.oracle_lb_init_shear.argtypes = [pp, ctypes.c_double, ctypes.c_double, dp]
     lib.oracle_dvm_run.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int, dp, dp, dp]
+    lib.oracle_dvm_run_forced.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp,
+                                          dp]
     lib.oracle_dvm_dt.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double]
     lib.oracle_dvm_dt.restype = ctypes.c_double
     return lib
@@ -210,8 +213,9 @@ class Problem:
 
 
 def run_dvm(n_nodes: int, nx: int, kn: float, u0: float, nsteps: int, cfl: float = 0.5,
-            kn_convention: str = "lambda"):
-    """Reduced linearised-BGK DVM with an n-point Gauss-Hermite rule.
+            kn_convention: str = "lambda", force_amp: float = 0.0, force_freq: float = 0.0):
+    """Reduced linearised-BGK DVM with an n-point Gauss-Hermite rule, free
+    (force_amp = 0) or driven by g = force_amp sin(x_i) cos(force_freq t).
 
     Returns (t, A, S) arrays of length nsteps + 1.
     """
@@ -221,7 +225,8 @@ def run_dvm(n_nodes: int, nx: int, kn: float, u0: float, nsteps: int, cfl: float
     t = np.empty(nsteps + 1)
     A = np.empty(nsteps + 1)
     S = np.empty(nsteps + 1)
-    rc = _load().oracle_dvm_run(nx, n_nodes, _dp(g), _dp(wg), tau, cfl, u0, nsteps, _dp(t), _dp(A), _dp(S))
+    rc = _load().oracle_dvm_run_forced(nx, n_nodes, _dp(g), _dp(wg), tau, cfl, u0, float(force_amp),
+                                       float(force_freq), nsteps, _dp(t), _dp(A), _dp(S))
     if rc != 0:
         raise RuntimeError("oracle_dvm_run failed")
     return t, A, S

@@ -1,7 +1,6 @@
 /*
  * Oracle: discrete velocity method for the linearised BGK equation of the
- * unforced standing shear wave, in the reduced form of Sec. 3.3 (Eqs. LBGK,
- * ga, gb) with the force set to zero.
+ * standing shear wave, in the reduced form of Sec. 3.3 (Eqs. LBGK, ga, gb).
  *
  * TEST INFRASTRUCTURE ONLY (loaded by tests/ and bench.py's CPU leg only).
  *
@@ -11,18 +10,51 @@
  *     dG/dt + xi_k dG/dx = (u - G) / tau,     u(x) = sum_k w_k G(x, xi_k)
  * (the velocity moment over the unit Gaussian, which is how the paper's
  * u = (1/sqrt(2 pi)) int G dxi reads once the Gaussian factor of the moment is
- * restored).  The other reduced function of Eq. ga decouples and stays zero.
+ * restored).  The other reduced function G_a of Eq. ga obeys a homogeneous
+ * equation, starts at zero and stays zero, so the force term g (G_a + 1) of
+ * Eq. gb is the body force g(x, t) = A_f sin(x_i) cos(phi t) itself:
+ *     dG/dt + xi_k dG/dx = (u - G) / tau + g.
  * Space-time discretisation, independent of the lattice: Strang splitting of
- * the relaxation (integrated exactly, u is invariant under it) around one
- * Lax-Wendroff advection step, dt = cfl * dx / max|xi_k|.
+ * the relaxation and force (integrated exactly: u gains int g dt, since
+ * sum w_k = 1, and G - u decays by exp(-h / tau)) around one Lax-Wendroff
+ * advection step, dt = cfl * dx / max|xi_k|.
  * Observables: A = 2/nx sum u sin(x_i), S = 2/nx sum sigma cos(x_i),
  * sigma = sum_k w_k xi_k G (the xy pressure-tensor moment).
  */
 #include <math.h>
 #include <stdlib.h>
 
-int oracle_dvm_run(int nx, int nv, const double *xi, const double *w, double tau, double cfl,
-                   double u0, int nsteps, double *t_out, double *A_out, double *S_out)
+/* Test builds only (tests/test_oracle_planted.py): ORACLE_PLANT = 8 drives with -g. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+
+/* int_{t0}^{t0 + h} cos(phi t) dt */
+static double cos_integral(double phi, double t0, double h)
+{
+    if (phi == 0.0) return h;
+    return (sin(phi * (t0 + h)) - sin(phi * t0)) / phi;
+}
+
+/* relaxation and force over [t0, t0 + h], exactly: u += A_f sin(x) int cos,
+ * G = u + (G - u) exp(-h / tau) */
+static void relax_force(double *G, double *u, int nx, int nv, double dx, double decay, double force_amp,
+                        double force_freq, double t0, double h)
+{
+    double c = (ORACLE_PLANT == 8 ? -force_amp : force_amp) * cos_integral(force_freq, t0, h);
+    for (int i = 0; i < nx; ++i) {
+        double un = u[i] + c * sin(i * dx);
+        for (int k = 0; k < nv; ++k) {
+            double *g = &G[(size_t)k * nx + i];
+            *g = un + (*g - u[i]) * decay;
+        }
+        u[i] = un;
+    }
+}
+
+int oracle_dvm_run_forced(int nx, int nv, const double *xi, const double *w, double tau, double cfl,
+                          double u0, double force_amp, double force_freq, int nsteps, double *t_out,
+                          double *A_out, double *S_out)
 {
     if (nx < 3 || nv < 1 || nsteps < 0 || cfl <= 0.0 || cfl > 1.0) return -1;
     const double pi = 3.14159265358979323846;
@@ -58,12 +90,8 @@ int oracle_dvm_run(int nx, int nv, const double *xi, const double *w, double tau
         if (A_out) A_out[s] = 2.0 * A / nx;
         if (S_out) S_out[s] = 2.0 * S / nx;
         if (s == nsteps) break;
-        /* half relaxation, advection, half relaxation */
-        for (int k = 0; k < nv; ++k)
-            for (int i = 0; i < nx; ++i) {
-                double *g = &G[(size_t)k * nx + i];
-                *g = u[i] + (*g - u[i]) * decay_half;
-            }
+        /* half relaxation (with the force), advection, half relaxation (with the force) */
+        relax_force(G, u, nx, nv, dx, decay_half, force_amp, force_freq, s * dt, 0.5 * dt);
         for (int k = 0; k < nv; ++k) {
             double C = xi[k] * dt / dx;
             double *g = &G[(size_t)k * nx];
@@ -78,16 +106,18 @@ int oracle_dvm_run(int nx, int nv, const double *xi, const double *w, double tau
             for (int k = 0; k < nv; ++k) ui += w[k] * G[(size_t)k * nx + i];
             u[i] = ui;
         }
-        for (int k = 0; k < nv; ++k)
-            for (int i = 0; i < nx; ++i) {
-                double *g = &G[(size_t)k * nx + i];
-                *g = u[i] + (*g - u[i]) * decay_half;
-            }
+        relax_force(G, u, nx, nv, dx, decay_half, force_amp, force_freq, (s + 0.5) * dt, 0.5 * dt);
     }
     free(G);
     free(Gn);
     free(u);
     return 0;
+}
+
+int oracle_dvm_run(int nx, int nv, const double *xi, const double *w, double tau, double cfl,
+                   double u0, int nsteps, double *t_out, double *A_out, double *S_out)
+{
+    return oracle_dvm_run_forced(nx, nv, xi, w, tau, cfl, u0, 0.0, 0.0, nsteps, t_out, A_out, S_out);
 }
 
 /* time step used by oracle_dvm_run for the same arguments */

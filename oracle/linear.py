@@ -118,6 +118,17 @@ def dvm_decay_rate(xi1d, w1d, tau, k=1.0):
     return float(-np.max(s.real))
 
 
+def dvm_forced_response(xi1d, w1d, tau, phi, k=1.0):
+    """Periodic response H of the continuous reduced DVM (Sec. 3.3, Eq. gb with
+    G_a = 0) to g = Re(e^{i phi t}) sin(k x): u -> Re(H e^{i phi t}) sin(k x).
+    For the mode, G_k (i phi + i k xi_k + 1/tau) = u / tau + 1, so with
+    S1 = sum_k w_k / (i phi + i k xi_k + 1/tau), H = S1 / (1 - S1 / tau)."""
+    xi1d = np.asarray(xi1d, dtype=np.float64)
+    w1d = np.asarray(w1d, dtype=np.float64)
+    s1 = np.sum(w1d / (1j * phi + 1j * k * xi1d + 1.0 / tau))
+    return complex(s1 / (1.0 - s1 / tau))
+
+
 def _projection(xi, w, isothermal):
     Q = w.size
     Pm = np.ones((Q, Q)) + np.einsum("ai,bi->ab", xi, xi)

@@ -157,6 +157,9 @@ def _load() -> ctypes.CDLL:
         "lb_server_last_error": (ctypes.c_char_p, [H]),
         "lb_dvm_run": (ctypes.c_int, [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_void_p]),
+        "lb_dvm_run_forced": (ctypes.c_int, [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp,
+                                             dp, ctypes.c_void_p]),
         "lb_solve_static": (ctypes.c_int, [ctypes.POINTER(lb_instance_desc), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                            ctypes.POINTER(lb_instance_state), ctypes.c_void_p]),
@@ -183,6 +186,7 @@ EXPORTS = [
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
     "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static", "lb_dvm_run",
+    "lb_dvm_run_forced",
 ]
 
 
@@ -337,6 +341,17 @@ def lb_dvm_run(taus, n_nodes: int, nx: int, u0: float, nsteps: int, cfl: float =
     shear = np.empty((tau.size, nsteps + 1))
     check(lib.lb_dvm_run(tau.size, _dptr(tau), n_nodes, nx, cfl, u0, nsteps, _dptr(amp), _dptr(shear),
                          stream or None))
+    return amp, shear
+
+
+def lb_dvm_run_forced(taus, n_nodes: int, nx: int, u0: float, force_amp: float, force_freq: float, nsteps: int,
+                      cfl: float = 0.5, stream: int = 0):
+    """GPU DVM driven by g = force_amp sin(x) cos(force_freq t); returns (A, S) as lb_dvm_run."""
+    tau = np.ascontiguousarray(np.atleast_1d(np.asarray(taus, dtype=np.float64)))
+    amp = np.empty((tau.size, nsteps + 1))
+    shear = np.empty((tau.size, nsteps + 1))
+    check(lib.lb_dvm_run_forced(tau.size, _dptr(tau), n_nodes, nx, cfl, u0, force_amp, force_freq, nsteps,
+                                _dptr(amp), _dptr(shear), stream or None))
     return amp, shear
 
 

@@ -1,11 +1,15 @@
 // Discrete velocity method (DVM) for the linearised BGK equation of the standing
-// shear wave, in the reduced form of Sec. 3.3 (Eqs. LBGK, ga, gb) with the force set
-// to zero: the unknown G(x, xi_k, t) at the nodes xi_k of an n-point Gauss-Hermite
-// rule obeys dG/dt + xi_k dG/dx = (u - G) / tau with u = sum_k w_k G_k.
+// shear wave, in the reduced form of Sec. 3.3 (Eqs. LBGK, ga, gb): the unknown
+// G(x, xi_k, t) at the nodes xi_k of an n-point Gauss-Hermite rule obeys
+// dG/dt + xi_k dG/dx = (u - G) / tau + g with u = sum_k w_k G_k and the body force
+// g(x, t) = A_f sin(x_i) cos(phi t) (0 for the free wave).  The other reduced function
+// (Eq. ga) is homogeneous, starts at zero and stays zero, so the force term of Eq. gb,
+// g (G_a + 1), is g itself.
 //
 // Space-time discretisation (independent of the lattice; the paper solves the DVM with
-// Lax-Wendroff): Strang splitting of the relaxation, integrated exactly (u is invariant
-// under it), around one Lax-Wendroff advection step; dt = cfl dx / max|xi_k|.
+// Lax-Wendroff): Strang splitting of the relaxation and force, integrated exactly (u gains
+// int g dt since sum w_k = 1; G - u decays by exp(-h / tau)), around one Lax-Wendroff
+// advection step; dt = cfl dx / max|xi_k|.
 // Observables per level: A = 2/nx sum u sin(x_i), S = 2/nx sum sigma cos(x_i),
 // sigma = sum_k w_k xi_k G.
 //
@@ -31,6 +35,7 @@ constexpr int kDvmThreads = 256;
 struct DvmArgs {
     int nx, nv, nsteps, n_inst;
     double dx, dt, u0;
+    double force_amp, force_freq;
     const double* tau;   // n_inst collision times
     double* amp;         // n_inst x (nsteps + 1)
     double* shear;
@@ -47,6 +52,13 @@ __device__ double block_sum(double v, double* red) {
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];  // fixed order
     return s;  // valid in thread 0
+}
+
+// A_f int_{t0}^{t0 + h} cos(phi t) dt
+__device__ double force_integral(const DvmArgs& A, double t0, double h) {
+    if (A.force_amp == 0.0) return 0.0;
+    if (A.force_freq == 0.0) return A.force_amp * h;
+    return A.force_amp * (sin(A.force_freq * (t0 + h)) - sin(A.force_freq * t0)) / A.force_freq;
 }
 
 __global__ void __launch_bounds__(kDvmThreads) lb_dvm_kernel(const __grid_constant__ DvmArgs A) {
@@ -87,10 +99,12 @@ __global__ void __launch_bounds__(kDvmThreads) lb_dvm_kernel(const __grid_consta
         }
         if (s == A.nsteps) break;
         __syncthreads();
-        // half relaxation (u is invariant under it)
+        // half relaxation with the force over [t_s, t_s + dt/2]
+        const double c1 = force_integral(A, s * A.dt, 0.5 * A.dt);
         for (int idx = threadIdx.x; idx < nv * nx; idx += blockDim.x) {
-            const double ui = u[idx % nx];
-            G[idx] = ui + (G[idx] - ui) * decay_half;
+            const int i = idx % nx;
+            const double ui = u[i];
+            G[idx] = (ui + c1 * sin(i * A.dx)) + (G[idx] - ui) * decay_half;
         }
         __syncthreads();
         // Lax-Wendroff advection, node by node, periodic
@@ -105,16 +119,18 @@ __global__ void __launch_bounds__(kDvmThreads) lb_dvm_kernel(const __grid_consta
             for (int i = threadIdx.x; i < nx; i += blockDim.x) G[(size_t)k * nx + i] = row[i];
             __syncthreads();
         }
-        // second half relaxation about the advected u
+        // second half relaxation about the advected u, with the force over [t_s + dt/2, t_s + dt]
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double ui = 0.0;
             for (int k = 0; k < nv; ++k) ui += A.w[k] * G[(size_t)k * nx + i];
             u[i] = ui;
         }
         __syncthreads();
+        const double c2 = force_integral(A, (s + 0.5) * A.dt, 0.5 * A.dt);
         for (int idx = threadIdx.x; idx < nv * nx; idx += blockDim.x) {
-            const double ui = u[idx % nx];
-            G[idx] = ui + (G[idx] - ui) * decay_half;
+            const int i = idx % nx;
+            const double ui = u[i];
+            G[idx] = (ui + c2 * sin(i * A.dx)) + (G[idx] - ui) * decay_half;
         }
         __syncthreads();
     }
@@ -131,10 +147,18 @@ extern "C" {
 
 lb_status lb_dvm_run(int n_inst, const double* tau, int n_nodes, int nx, double cfl, double u0, int nsteps,
                      double* amp, double* shear, void* stream) {
+    return lb_dvm_run_forced(n_inst, tau, n_nodes, nx, cfl, u0, 0.0, 0.0, nsteps, amp, shear, stream);
+}
+
+lb_status lb_dvm_run_forced(int n_inst, const double* tau, int n_nodes, int nx, double cfl, double u0,
+                            double force_amp, double force_freq, int nsteps, double* amp, double* shear,
+                            void* stream) {
     if (n_inst < 1 || !tau || !amp || !shear) return dvm_fail(LB_ERR_ARG, "n_inst >= 1 and tau, amp, shear are required");
     if (n_nodes < 1 || n_nodes > kDvmMaxNodes) return dvm_fail(LB_ERR_ARG, "n_nodes must be in [1, 64]");
     if (nx < 3 || nsteps < 0 || !(cfl > 0.0 && cfl <= 1.0) || !std::isfinite(u0))
         return dvm_fail(LB_ERR_ARG, "nx >= 3, nsteps >= 0, 0 < cfl <= 1 and a finite u0 are required");
+    if (!std::isfinite(force_amp) || !std::isfinite(force_freq))
+        return dvm_fail(LB_ERR_ARG, "force_amp and force_freq must be finite");
     for (int i = 0; i < n_inst; ++i)
         if (!(tau[i] > 0.0) || !std::isfinite(tau[i])) return dvm_fail(LB_ERR_ARG, "collision times must be positive");
     const size_t smem = sizeof(double) * ((size_t)n_nodes * nx + 2 * (size_t)nx);
@@ -161,6 +185,8 @@ lb_status lb_dvm_run(int n_inst, const double* tau, int n_nodes, int nx, double 
     }
     A.dt = cfl * A.dx / (vmax > 0 ? vmax : 1.0);
     A.u0 = u0;
+    A.force_amp = force_amp;
+    A.force_freq = force_freq;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t rec = (size_t)n_inst * ((size_t)nsteps + 1);
     double *d_tau = nullptr, *d_out = nullptr;

@@ -5,7 +5,8 @@ while all of them hold for the oracle as it is.
 Planted mistakes: 1 sign of the force term; 2 no rho g dt/2 in the momentum; 3 force
 relaxed with omega instead of omega tau; 4 Lax-Wendroff streaming against xi; 5 the
 highest Hermite order dropped from the equilibrium; 6 sigma_xy without (1 - omega/2);
-7 the first-order scheme of Eq. slb relaxing with the second-order omega.
+7 the first-order scheme of Eq. slb relaxing with the second-order omega; 8 the driven
+DVM pushed by -g.
 """
 import numpy as np
 import pytest
@@ -82,7 +83,20 @@ def _p_l1():
     return abs(oracle.decay_fit(d[:, 0], d[:, 4], 1.0) / (P.tau - 0.5 * P.dt) - 1) < 1e-3
 
 
-PINS = {"P-c": _p_c, "P-e": _p_e, "P-j1": _p_j1, "P-j2": _p_j2, "P-j3": _p_j3, "P-k1": _p_k1, "P-l1": _p_l1}
+def _p_m2():
+    """The driven DVM reaches the continuous reduced-DVM response (Sec. 3.3)."""
+    amp, phi, n, kn, nx = 1e-4, 1.0, 8, 0.5, 64
+    g, w = oracle.quadrature.gauss_hermite(n)
+    dt = oracle.dvm_dt(n, nx)
+    t, A, _ = oracle.run_dvm(n, nx, kn, 0.0, int(30.0 / dt), kn_convention="paper", force_amp=amp, force_freq=phi)
+    sel = t >= t[-1] - 4 * np.pi / phi
+    X = np.stack([np.cos(phi * t[sel]), np.sin(phi * t[sel])], axis=1)
+    (a, b), *_ = np.linalg.lstsq(X, A[sel], rcond=None)
+    return abs((a - 1j * b) / amp / linear.dvm_forced_response(g, w, kn, phi) - 1) < 3e-3
+
+
+PINS = {"P-c": _p_c, "P-e": _p_e, "P-j1": _p_j1, "P-j2": _p_j2, "P-j3": _p_j3, "P-k1": _p_k1, "P-l1": _p_l1,
+        "P-m2": _p_m2}
 
 
 def test_all_pins_hold_for_the_oracle():
@@ -97,6 +111,7 @@ def test_all_pins_hold_for_the_oracle():
     (5, {"P-c", "P-k1"}),
     (6, {"P-e"}),
     (7, {"P-l1"}),
+    (8, {"P-m2"}),
 ])
 def test_planted_mistake_is_caught(plant, expect_failing):
     with oracle.planted(plant):
