@@ -142,9 +142,10 @@ def ncu_traffic(quad):
 
 def workload_name(args):
     if (args.n == 4096 and args.quad == "D2Q36-GH" and args.n_eq == 3 and args.precision == "f32"
-            and args.scheme == "second_order"):
+            and args.scheme == "second_order" and args.streaming == "lax_wendroff"):
         return WORKLOAD
     scheme = ", first-order scheme (Eq. slb)" if args.scheme == "first_order" else ""
+    scheme += ", second-order upwind streaming" if args.streaming == "upwind2" else ""
     return (f"standing shear wave {args.n}x{args.n}, {args.quad}, N={args.n_eq}, {args.precision} deviations, "
             f"Kn={args.kn}{scheme}")
 
@@ -183,9 +184,12 @@ def dvm_crosscheck(capi, Lattice, args, n=256, t_end=6.0):
 
 
 def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32",
-                    scheme="second_order"):
+                    scheme="second_order", streaming="lax_wendroff"):
     stream = torch.cuda.Stream()
-    L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream, scheme=scheme)
+    if not quad.endswith("-GH"):
+        streaming = "lax_wendroff"  # on-lattice sets stream by the exact shift
+    L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream, scheme=scheme,
+                streaming=streaming)
     L.init_shear_wave(1e-3, 1e-3)
     L.step(warmup)
     L.synchronize()
@@ -224,7 +228,7 @@ def run_gpu(args):
         if not quad:
             continue
         L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn,
-                                                  args.n_eq, args.precision, args.scheme)
+                                                  args.n_eq, args.precision, args.scheme, args.streaming)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -347,11 +351,12 @@ def run_gpu(args):
 
 # ----------------------------------------------------------------------------- oracle (CPU) legs
 
-def oracle_sample(quad, rows, steps, kn, n_eq=3, scheme="second_order"):
+def oracle_sample(quad, rows, steps, kn, n_eq=3, scheme="second_order", streaming="lax_wendroff"):
     import oracle
 
     oracle.build()
-    P = oracle.Problem(quad, n_eq, 4096, rows, kn, scheme=scheme)
+    P = oracle.Problem(quad, n_eq, 4096, rows, kn, scheme=scheme,
+                       streaming=streaming if quad.endswith("-GH") else "lax_wendroff")
     f = P.init_shear(1e-3, 1e-3)
     t0 = time.perf_counter()
     P.run(f, steps, record=True)
@@ -360,7 +365,8 @@ def oracle_sample(quad, rows, steps, kn, n_eq=3, scheme="second_order"):
 
 
 def cpu_baseline(args):
-    mlups, el = oracle_sample(args.quad, args.cpu_rows, args.cpu_steps, args.kn, args.n_eq, args.scheme)
+    mlups, el = oracle_sample(args.quad, args.cpu_rows, args.cpu_steps, args.kn, args.n_eq, args.scheme,
+                              args.streaming)
     return {"value": round(mlups, 5), "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle, {args.quad} N={args.n_eq}, periodic 4096x{args.cpu_rows} slab of the workload, "
                       f"{args.cpu_steps} steps with records ({el:.1f} s), single thread"}
@@ -719,6 +725,7 @@ def main():
     ap.add_argument("--n-eq", type=int, default=3)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--scheme", default="second_order", choices=["second_order", "first_order"])
+    ap.add_argument("--streaming", default="lax_wendroff", choices=["lax_wendroff", "upwind2"])
     ap.add_argument("--kn", type=float, default=0.1)
     ap.add_argument("--e2e-steps", type=int, default=0, help="levels of the end-to-end leg (0: --steps)")
     ap.add_argument("--cpu-rows", type=int, default=48)

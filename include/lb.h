@@ -90,6 +90,16 @@ typedef enum { LB_KN_LAMBDA = 0, LB_KN_PAPER = 1 } lb_kn_convention;
  *   the velocity set's own in both (exact shift, or Lax-Wendroff off-lattice). */
 typedef enum { LB_SCHEME_SECOND_ORDER = 0, LB_SCHEME_FIRST_ORDER = 1 } lb_scheme;
 
+/* Streaming of the off-lattice (Gauss-Hermite product) sets.
+ * LAX_WENDROFF (default): 1-D Lax-Wendroff along x then y (the scheme named in
+ *   Sec. 3.3); on-lattice sets always stream by the exact shift.
+ * UPWIND2: 1-D second-order upwind (Beam-Warming) along x then y, from the cell and
+ *   its two upstream neighbours: out_i = f_i - c/2 (3 f_i - 4 f_{i-s} + f_{i-2s})
+ *   + c^2/2 (f_i - 2 f_{i-s} + f_{i-2s}), c = |C|, s = sign(C), C = xi dt/dx
+ *   (exact shift at c = 1).  Off-lattice sets with F32/F64 storage only
+ *   (LB_ERR_UNSUPPORTED otherwise); steps run the plain-load kernel. */
+typedef enum { LB_STREAM_LAX_WENDROFF = 0, LB_STREAM_UPWIND2 = 1 } lb_streaming;
+
 typedef struct {
     lb_quadrature quadrature;
     int n_eq;                  /* Hermite order N of the equilibrium, 1..4.  N = 1 is the
@@ -126,6 +136,7 @@ typedef struct {
      * LB_ERR_TIMEOUT; the context stays usable.  0 (default) in normal use. */
     int test_withhold_stage;
     lb_scheme scheme;          /* default LB_SCHEME_SECOND_ORDER */
+    lb_streaming streaming;    /* default LB_STREAM_LAX_WENDROFF */
 } lb_params;
 
 /* One diagnostics record per time level n (t = n dt), FP64 sums over the grid:

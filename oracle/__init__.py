@@ -76,7 +76,7 @@ class _Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("isothermal", ctypes.c_int), ("ninner", ctypes.c_int),
         ("zin", ctypes.POINTER(ctypes.c_double)), ("win", ctypes.POINTER(ctypes.c_double)),
         ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double), ("force_uniform", ctypes.c_int),
-        ("scheme", ctypes.c_int),
+        ("scheme", ctypes.c_int), ("streaming", ctypes.c_int),
     ]
 
 
@@ -140,12 +140,13 @@ class Problem:
     (force_uniform: g_y = force_amp cos(force_freq t)); force_amp = 0 is the free wave.
     N: Hermite order of the equilibrium, 1..4.
     scheme: "second_order" (Eq. 2order) or "first_order" (the standard LB of Eq. slb,
-    omega = dt / tau, no dt/2 corrections of the moments, sigma_xy without 1 - omega/2)."""
+    omega = dt / tau, no dt/2 corrections of the moments, sigma_xy without 1 - omega/2).
+    streaming (off-lattice sets): "lax_wendroff" or "upwind2" (second-order upwind)."""
 
     def __init__(self, set_name: str, N: int, nx: int, ny: int, kn: float,
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
                  force_amp: float = 0.0, force_freq: float = 0.0, force_uniform: bool = False,
-                 scheme: str = "second_order"):
+                 scheme: str = "second_order", streaming: str = "lax_wendroff"):
         self.vs = quadrature.velocity_set(set_name)
         self.set_name, self.N, self.nx, self.ny, self.kn = set_name, N, nx, ny, kn
         self.isothermal = isothermal
@@ -159,6 +160,9 @@ class Problem:
         if scheme not in ("second_order", "first_order"):
             raise ValueError(scheme)
         self.scheme = scheme
+        if streaming not in ("lax_wendroff", "upwind2"):
+            raise ValueError(streaming)
+        self.streaming = streaming
         if scheme == "first_order":
             self.omega = self.dt / self.tau  # Eq. slb
         else:
@@ -172,7 +176,7 @@ class Problem:
                           self._e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if self._e is not None else None,
                           self.dx, self.dt, self.tau, 1.0, int(isothermal), INNER_NODES,
                           _dp(self._z), _dp(self._wz), float(force_amp), float(force_freq),
-                          int(force_uniform), int(scheme == "first_order"))
+                          int(force_uniform), int(scheme == "first_order"), int(streaming == "upwind2"))
 
     @property
     def Q(self):

@@ -27,7 +27,12 @@
  *   stream      on-lattice: f~_alpha(r + xi_alpha dt) = f*_alpha(r), an exact
  *               periodic shift by e_alpha (Sec. 2.3); off-lattice: Lax-Wendroff
  *               along x then along y (the scheme named in Sec. 3.3 and the
- *               caption of the D2Q400 figure), periodic.
+ *               caption of the D2Q400 figure), periodic; or (streaming = 1) the
+ *               second-order upwind (Beam-Warming) scheme along x then y, which
+ *               uses the two upstream neighbours:
+ *               out_i = f_i - C/2 (3 f_i - 4 f_{i-s} + f_{i-2s})
+ *                             + C^2/2 (f_i - 2 f_{i-s} + f_{i-2s}),  s = sign(C),
+ *               with |C| in place of C.
  * First-order scheme (scheme = 1, the standard LB of Eq. slb, Sec. 2.2): the state is
  * f itself and one step is f(r + xi dt, t + dt) = f - (dt/tau)(f - f^eq) + dt g_alpha,
  * i.e. the collide line above with omega = dt / tau (so omega tau = dt), moments
@@ -51,6 +56,7 @@
 #endif
 #define PLANTED(k) (ORACLE_PLANT == (k))
 /* planted 7: the first-order scheme relaxes with the second-order omega */
+/* planted 9: second-order upwind streaming from the downstream side */
 
 #define ORACLE_MAXQ 128
 #define ORACLE_MAXN 4
@@ -72,6 +78,7 @@ typedef struct {
     double force_freq;   /* phi */
     int force_uniform;   /* 1: s(x) = 1, 0: s(x) = sin(x_i) */
     int scheme;          /* 0: Eq. 2order, 1: Eq. slb (first order) */
+    int streaming;       /* off-lattice: 0 Lax-Wendroff, 1 second-order upwind */
 } oracle_lb_params;
 
 /* relaxation rate of the scheme */
@@ -267,6 +274,21 @@ static void lax_wendroff_line(const double *in, double *out, int n, size_t s, do
     }
 }
 
+/* Second-order upwind (Beam-Warming) update of one periodic line, read with stride s:
+ * the two neighbours on the upstream side of the Courant number C. */
+static void upwind2_line(const double *in, double *out, int n, size_t s, double C)
+{
+    int up = C >= 0.0 ? -1 : 1; /* direction of the upstream neighbours */
+    if (PLANTED(9)) up = -up;   /* planted 9: the downstream neighbours */
+    double c = fabs(C);
+    for (int i = 0; i < n; ++i) {
+        double f0 = in[(size_t)i * s];
+        double f1 = in[(size_t)(((i + up) % n + n) % n) * s];
+        double f2 = in[(size_t)(((i + 2 * up) % n + n) % n) * s];
+        out[(size_t)i * s] = f0 - 0.5 * c * (3.0 * f0 - 4.0 * f1 + f2) + 0.5 * c * c * (f0 - 2.0 * f1 + f2);
+    }
+}
+
 static void stream(const oracle_lb_params *p, const double *fstar, double *fnew, double *tmp)
 {
     const int nx = p->nx, ny = p->ny;
@@ -286,10 +308,12 @@ static void stream(const oracle_lb_params *p, const double *fstar, double *fnew,
         } else {
             double Cx = p->xi[2 * a] * p->dt / p->dx;
             double Cy = p->xi[2 * a + 1] * p->dt / p->dx; /* dy = dx */
+            void (*line)(const double *, double *, int, size_t, double) =
+                p->streaming == 1 ? upwind2_line : lax_wendroff_line;
             for (int y = 0; y < ny; ++y)
-                lax_wendroff_line(src + (size_t)y * nx, tmp + (size_t)y * nx, nx, 1, Cx);
+                line(src + (size_t)y * nx, tmp + (size_t)y * nx, nx, 1, Cx);
             for (int x = 0; x < nx; ++x)
-                lax_wendroff_line(tmp + x, dst + x, ny, (size_t)nx, Cy);
+                line(tmp + x, dst + x, ny, (size_t)nx, Cy);
         }
     }
 }

@@ -33,7 +33,23 @@ from __future__ import annotations
 import numpy as np
 
 
-def lb_mode_matrix(xi, w, omega, dx, dt, k=1.0, e=None, isothermal=False):
+def stream_symbol(xi, dx, dt, k=1.0, e=None, streaming="lax_wendroff"):
+    """Fourier symbol S_a(k) of one streaming step for the mode exp(i k x): the exact
+    shift, Lax-Wendroff, or second-order upwind (Beam-Warming: with c = |C| and
+    z = exp(-i s theta), s = sign(C), S = 1 - c/2 (3 - 4 z + z^2) + c^2/2 (1 - z)^2)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    theta = k * dx
+    if e is not None:
+        return np.exp(-1j * k * np.asarray(e)[:, 0] * dx)
+    C = xi[:, 0] * dt / dx
+    if streaming == "upwind2":
+        c = np.abs(C)
+        z = np.exp(-1j * np.where(C >= 0, 1.0, -1.0) * theta)
+        return 1.0 - 0.5 * c * (3.0 - 4.0 * z + z * z) + 0.5 * c * c * (1.0 - z) ** 2
+    return 1.0 - 1j * C * np.sin(theta) - C * C * (1.0 - np.cos(theta))
+
+
+def lb_mode_matrix(xi, w, omega, dx, dt, k=1.0, e=None, isothermal=False, streaming="lax_wendroff"):
     xi = np.asarray(xi, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     Q = w.size
@@ -43,21 +59,17 @@ def lb_mode_matrix(xi, w, omega, dx, dt, k=1.0, e=None, isothermal=False):
         s2 = 0.5 * np.sum(xi * xi, axis=1) - 1.0
         P += np.outer(s2, s2)
     P = w[:, None] * P
-    theta = k * dx
-    if e is not None:
-        S = np.exp(-1j * k * np.asarray(e)[:, 0] * dx)
-    else:
-        C = xi[:, 0] * dt / dx
-        S = 1.0 - 1j * C * np.sin(theta) - C * C * (1.0 - np.cos(theta))
+    S = stream_symbol(xi, dx, dt, k, e, streaming)
     return S[:, None] * ((1.0 - omega) * np.eye(Q) + omega * P)
 
 
-def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False, scheme="second_order"):
+def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False, scheme="second_order",
+                      streaming="lax_wendroff"):
     """A(n) and S(n), n = 0..nsteps, of the linearised scheme from u_y = u0 sin x.
     scheme "first_order" (Eq. slb) reads sigma_xy without the factor 1 - omega/2."""
     xi = np.asarray(xi, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
-    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
+    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal, streaming)
     # e^{ix} coefficient of the initial equilibrium deviation w_a xi_ay u0 sin x
     f = w * xi[:, 1] * (u0 / 2j)
     Q = w.size
@@ -79,10 +91,10 @@ def lb_linear_history(xi, w, omega, dx, dt, u0, nsteps, e=None, isothermal=False
     return A, S
 
 
-def lb_decay_rate(xi, w, omega, dx, dt, e=None, isothermal=False):
+def lb_decay_rate(xi, w, omega, dx, dt, e=None, isothermal=False, streaming="lax_wendroff"):
     """-ln|lambda|/dt of the least-damped eigenvalue carrying shear (u_y) content."""
     xi = np.asarray(xi, dtype=np.float64)
-    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal)
+    M = lb_mode_matrix(xi, w, omega, dx, dt, 1.0, e, isothermal, streaming)
     lam, V = np.linalg.eig(M)
     shear = np.abs(xi[:, 1] @ V)
     ok = shear > 1e-8 * shear.max()

@@ -31,6 +31,8 @@ PRECISIONS = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
 KN_LAMBDA, KN_PAPER = 0, 1
 # lb_scheme
 SCHEMES = {"second_order": 0, "first_order": 1}
+# lb_streaming
+STREAMINGS = {"lax_wendroff": 0, "upwind2": 1}
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -44,7 +46,7 @@ class lb_params(ctypes.Structure):
         ("storage_scale", ctypes.c_double), ("step_kernel", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
         ("force_amp", ctypes.c_double), ("force_freq", ctypes.c_double),
-        ("test_withhold_stage", ctypes.c_int), ("scheme", ctypes.c_int),
+        ("test_withhold_stage", ctypes.c_int), ("scheme", ctypes.c_int), ("streaming", ctypes.c_int),
     ]
 
 

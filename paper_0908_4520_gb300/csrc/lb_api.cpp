@@ -234,6 +234,7 @@ lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int ra
     lbk::Launch L;
     L.kind = kind;
     L.n_eq = h->p.n_eq;
+    L.upwind = h->p.streaming == LB_STREAM_UPWIND2;
     L.grid = grid;
     L.stream = h->stream;
     L.args = &A;
@@ -376,6 +377,7 @@ void lb_params_default(lb_params* p) {
     p->force_freq = 0.0;
     p->test_withhold_stage = 0;
     p->scheme = LB_SCHEME_SECOND_ORDER;
+    p->streaming = LB_STREAM_LAX_WENDROFF;
 }
 
 const char* lb_status_string(lb_status s) {
@@ -443,6 +445,13 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     if (P.n_eq < 1 || P.n_eq > 4) return reject(LB_ERR_ARG, "n_eq must be 1, 2, 3 or 4");
     if (P.scheme != LB_SCHEME_SECOND_ORDER && P.scheme != LB_SCHEME_FIRST_ORDER)
         return reject(LB_ERR_ARG, "unknown scheme");
+    if (P.streaming != LB_STREAM_LAX_WENDROFF && P.streaming != LB_STREAM_UPWIND2)
+        return reject(LB_ERR_ARG, "unknown streaming");
+    const bool upwind = P.streaming == LB_STREAM_UPWIND2;
+    if (upwind && (P.precision == LB_BF16 || P.precision == LB_F16))
+        return reject(LB_ERR_UNSUPPORTED, "second-order upwind streaming is built for F32/F64 storage");
+    if (upwind && P.step_kernel == 2)
+        return reject(LB_ERR_UNSUPPORTED, "second-order upwind streaming runs the plain-load kernel");
     if (!(P.kn > 0) || !std::isfinite(P.kn)) return reject(LB_ERR_ARG, "kn must be positive");
     if (!(P.cfl > 0 && P.cfl <= 1.0)) return reject(LB_ERR_ARG, "cfl must be in (0, 1]");
     if (P.diag_capacity < 1) return reject(LB_ERR_ARG, "diag_capacity must be >= 1");
@@ -472,6 +481,18 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
                                               ? "16-bit storage is built for the Gauss-Hermite product sets only"
                                               : "this (quadrature, precision) unit is not in the build");
     }
+    if (upwind && h->vs.on_lattice) {
+        delete h;
+        return reject(LB_ERR_ARG, "on-lattice sets stream by the exact shift; upwind streaming is for the "
+                                  "Gauss-Hermite product sets");
+    }
+    if (upwind) {  // the kernel takes the upstream side from the node's index: ascending, symmetric nodes
+        for (int i = 0; i < h->vs.na; ++i)
+            if ((h->vs.axis[i] < 0) != (i < h->vs.na / 2)) {
+                delete h;
+                return reject(LB_ERR_UNSUPPORTED, "axis nodes not in ascending symmetric order");
+            }
+    }
     h->dx = 2.0 * M_PI / P.nx;
     double amax = 0;
     for (double a : h->vs.axis) amax = std::max(amax, std::fabs(a));
@@ -500,7 +521,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         }
     }
     const int tw = 32 * h->shape.V;
-    h->gy = h->vs.halo;
+    h->gy = upwind ? std::max(h->vs.halo, 2) : h->vs.halo;  // upwind: two upstream rows
     h->pitch = (P.nx + 2 * lbk::kGhostX + 63) / 64 * 64 + LB_PITCH_PAD;
     h->plane = (long long)h->pitch * (P.ny + 2 * h->gy);
     h->origin = (long long)h->gy * h->pitch + lbk::kGhostX;
@@ -531,7 +552,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         delete h;
         return reject(LB_ERR_UNSUPPORTED, "the TMA-staged step kernel runs the free wave; forced runs use the plain kernel");
     }
-    if (h->shape.tma && P.force_amp == 0.0) {
+    if (h->shape.tma && P.force_amp == 0.0 && !upwind) {
         const int ttw = h->shape.tma_tw;
         h->tma_ntiles_x = (P.nx + ttw - 1) / ttw;
         h->tma_x0_last = P.nx >= ttw ? P.nx - ttw : 0;

@@ -29,6 +29,7 @@ struct Tab {
     R hn[kMaxNA][kMaxN + 1];  // He_k(a_i) / k!
     R whn[kMaxNA][kMaxN + 1]; // W_i He_k(a_i) / k!
     R lw[kMaxNA][3];          // Lax-Wendroff weights of f*(x-1), f*(x), f*(x+1)
+    R uw[kMaxNA][3];          // second-order upwind weights of f*(x-2s), f*(x-s), f*(x), s = sign(a_i)
     R w[kMaxQ];               // quadrature weights
     R winv[kMaxQ];            // 1 / w
     R xixy[kMaxQ];            // xi_x xi_y
@@ -98,6 +99,7 @@ struct Shape {
 struct Launch {
     int kind;                 // Kind
     int n_eq;                 // 1..4
+    int upwind;               // 1: second-order upwind streaming (off-lattice sets, 32/64-bit storage)
     int grid;                 // blocks (persistent grid-stride over tiles)
     cudaStream_t stream;
     const void* args;         // Args<float>/Args<double> matching the unit, or Shape* for kQueryShape

@@ -76,6 +76,16 @@ void build_tab(const VelocitySetInfo& vs, double dt, double dx, double scale, lb
         t.lw[i][0] = (R)l0;
         t.lw[i][1] = (R)(1.0 - l0 - l2);
         t.lw[i][2] = (R)l2;
+        // second-order upwind (Beam-Warming), c = |C|: the two upstream neighbours and the cell
+        const double c = std::fabs(C);
+        double u0 = 0.5 * c * (c - 1.0), u1 = c * (2.0 - c);
+        if (std::is_same<R, float>::value) {
+            u0 = snap_unit(u0);
+            u1 = snap_unit(u1);
+        }
+        t.uw[i][0] = (R)u0;
+        t.uw[i][1] = (R)u1;
+        t.uw[i][2] = (R)(1.0 - u0 - u1);
     }
     for (int a = 0; a < vs.q; ++a) {
         t.w[a] = (R)vs.w[a];

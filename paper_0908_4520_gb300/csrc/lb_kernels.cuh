@@ -1111,7 +1111,8 @@ __device__ __forceinline__ void finish_step(const Args<R>& A, const R (&acc)[6],
 // KIND = kStep:    f* (next level) into dst, diagnostics when due.
 // KIND = kStepForced: the same with the body force (lb_params.force_amp != 0).
 // KIND = kMoments: per-cell rho, u, T, sigma_xy (and optionally f~) of the level; no store.
-template <class VS, int N, class S, class R, int KIND>
+// UPW: off-lattice streaming by second-order upwind instead of Lax-Wendroff.
+template <class VS, int N, class S, class R, int KIND, bool UPW = false>
 __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
     lb_fused_kernel(const __grid_constant__ Args<R> A) {
     constexpr int Q = VS::Q;
@@ -1174,6 +1175,46 @@ __global__ void __launch_bounds__(Cfg<VS, S>::THREADS, Cfg<VS, S>::MINB)
                 } else {
                     ft[a] = ld1<S, R>(p, sc);
                 }
+            } else if constexpr (UPW) {
+                // tensor-product second-order upwind (Beam-Warming), one cell per lane: y pass
+                // over the cell's row and the two upstream rows, x pass by shuffles from the two
+                // upstream lanes; the two lanes at the warp's downstream edge compute the two
+                // upstream columns outside the warp
+                static_assert(V == 1 && !Is16<S>::value, "upwind streaming: one cell per lane, 32/64-bit");
+                constexpr int ix = VS::ix(a), iy = VS::iy(a);
+                constexpr int sx = VS::axis_sign(ix), sy = VS::axis_sign(iy);
+                const R yf = A.tab.uw[iy][0], yn = A.tab.uw[iy][1], ys = A.tab.uw[iy][2];
+                const R xf = A.tab.uw[ix][0], xn = A.tab.uw[ix][1], xs = A.tab.uw[ix][2];
+                const S* r0 = pl + (long long)y * A.pitch;
+                const S* rn = r0 - (long long)sy * A.pitch;
+                const S* rf = r0 - 2LL * sy * A.pitch;
+                const R one = R(1);
+                // lanes past the grid read the images of columns 0 and 1 (nx, nx + 1)
+                const int xu = min(g.x, A.nx + 1);
+                const R gv = fma(yf, ld1<S, R>(rf + xu, one), fma(yn, ld1<S, R>(rn + xu, one),
+                                                                 ys * ld1<S, R>(r0 + xu, one)));
+                // extra column: x0 - 2 + (lane & 1) (lanes 30, 31) for sx > 0,
+                // x0 + 32 + (lane & 1) (lanes 0, 1) for sx < 0, clamped into the rim
+                const int xe = sx > 0 ? x0 - 2 + (lane & 1) : min(x0 + 32 + (lane & 1), A.nx + 1);
+                const R ge = fma(yf, ld1<S, R>(rf + xe, one), fma(yn, ld1<S, R>(rn + xe, one),
+                                                                 ys * ld1<S, R>(r0 + xe, one)));
+                R g1, g2;
+                if constexpr (sx > 0) {
+                    g1 = __shfl_up_sync(0xffffffffu, gv, 1);
+                    g2 = __shfl_up_sync(0xffffffffu, gv, 2);
+                    const R e2 = __shfl_sync(0xffffffffu, ge, 30);  // column x0 - 2
+                    const R e1 = __shfl_sync(0xffffffffu, ge, 31);  // column x0 - 1
+                    if (lane == 0) { g1 = e1; g2 = e2; }
+                    if (lane == 1) g2 = e1;
+                } else {
+                    g1 = __shfl_down_sync(0xffffffffu, gv, 1);
+                    g2 = __shfl_down_sync(0xffffffffu, gv, 2);
+                    const R e1 = __shfl_sync(0xffffffffu, ge, 0);   // column x0 + 32
+                    const R e2 = __shfl_sync(0xffffffffu, ge, 1);   // column x0 + 33
+                    if (lane == 31) { g1 = e1; g2 = e2; }
+                    if (lane == 30) g2 = e1;
+                }
+                ft[a] = fma(xf, g2, fma(xn, g1, xs * gv));
             } else {
                 // tensor-product Lax-Wendroff: y pass in registers, x pass by shuffles;
                 // the warp's two edge lanes take their outer neighbour from one extra column
@@ -1575,6 +1616,29 @@ cudaError_t launch_typed(const Launch& L) {
         return cudaSuccess;
     }
     const Args<R>& A = *static_cast<const Args<R>*>(L.args);
+    // second-order upwind streaming: Lax-Wendroff sets with 32/64-bit storage, register kernel
+    constexpr bool kUpw = !VS::kOnLattice && !Is16<S>::value;
+    if (L.upwind) {
+        if constexpr (kUpw) {
+            switch (L.kind) {
+                case kStep:
+                    lb_fused_kernel<VS, N, S, R, kStep, true><<<L.grid, C::THREADS, 0, L.stream>>>(A);
+                    return cudaGetLastError();
+                case kStepForced:
+                    lb_fused_kernel<VS, N, S, R, kStepForced, true><<<L.grid, C::THREADS, 0, L.stream>>>(A);
+                    return cudaGetLastError();
+                case kMoments:
+                    lb_fused_kernel<VS, N, S, R, kMoments, true><<<L.grid, C::THREADS, 0, L.stream>>>(A);
+                    return cudaGetLastError();
+                case kInit:
+                    break;  // no streaming
+                default:
+                    return cudaErrorNotSupported;
+            }
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
     switch (L.kind) {
         case kStep:
             lb_fused_kernel<VS, N, S, R, kStep><<<L.grid, C::THREADS, 0, L.stream>>>(A);

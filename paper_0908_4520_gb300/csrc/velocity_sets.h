@@ -38,6 +38,8 @@ struct GaussHermiteProduct {
     static constexpr int kHalo = 1;
     LB_HD static constexpr int ix(int a) { return a / NQ1; }
     LB_HD static constexpr int iy(int a) { return a % NQ1; }
+    // sign of axis node i (the nodes are in ascending order and symmetric; NQ1 even)
+    LB_HD static constexpr int axis_sign(int i) { return i < NQ1 / 2 ? -1 : 1; }
     LB_HD static constexpr int axis_int(int) { return 0; }
     LB_HD static constexpr int ex(int) { return 0; }
     LB_HD static constexpr int ey(int) { return 0; }

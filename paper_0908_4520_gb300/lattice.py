@@ -20,13 +20,15 @@ class Lattice:
     n_eq: Hermite order N of the equilibrium, 1..4 (1: f^eq = w rho (1 + xi.u)).
     scheme: "second_order" (Eq. 2order, default) or "first_order" (the standard LB of
     Eq. slb: omega = dt / tau, state f, no dt/2 corrections).
+    streaming: "lax_wendroff" (default) or "upwind2" (second-order upwind; Gauss-Hermite
+    product sets, f32/f64).
     """
 
     def __init__(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, precision: str = "f32",
                  kn_convention: str = "lambda", cfl: float = 1.0, isothermal: bool = False,
                  diag_capacity: int = 65536, storage_scale: float = 0.0, stream: int | None = None,
                  step_kernel: str = "auto", force_amp: float = 0.0, force_freq: float = 0.0,
-                 test_withhold_stage: int = 0, scheme: str = "second_order"):
+                 test_withhold_stage: int = 0, scheme: str = "second_order", streaming: str = "lax_wendroff"):
         p = capi.lb_params_default()
         p.quadrature = capi.QUADRATURES[quadrature]
         p.n_eq, p.nx, p.ny, p.kn = n_eq, nx, ny, kn
@@ -41,6 +43,7 @@ class Lattice:
         p.force_amp, p.force_freq = force_amp, force_freq
         p.test_withhold_stage = int(test_withhold_stage)
         p.scheme = capi.SCHEMES[scheme]
+        p.streaming = capi.STREAMINGS[streaming]
         self.quadrature, self.n_eq, self.nx, self.ny = quadrature, n_eq, nx, ny
         self.h = capi.lb_create_ex(p)
         inf = capi.lb_get_info(self.h)

@@ -56,13 +56,17 @@ def test_status_strings(capi):
 def test_params_default(capi):
     p = capi.lb_params_default()
     assert p.precision == 0 and p.cfl == 1.0 and p.diag_capacity == 65536 and p.n_eq == 2
-    assert p.scheme == 0
+    assert p.scheme == 0 and p.streaming == 0
 
 
 @pytest.mark.parametrize("kw,status", [
     (dict(nx=63), -1), (dict(nx=0), -1), (dict(ny=0), -1), (dict(n_eq=5), -1), (dict(n_eq=0), -1),
     (dict(scheme=2), -1),
     (dict(scheme=1, kn=1e-3), -1),             # Eq. slb with tau <= dt/2 (omega >= 2)
+    (dict(streaming=2), -1),
+    (dict(streaming=1, quadrature=3), -1),     # on-lattice sets stream by the exact shift
+    (dict(streaming=1, precision=2), -2),      # upwind streaming: F32/F64 storage
+    (dict(streaming=1, step_kernel=2), -2),    # upwind streaming runs the plain-load kernel
     (dict(kn=0.0), -1), (dict(kn=-1.0), -1), (dict(cfl=1.5), -1), (dict(cfl=0.0), -1),
     (dict(quadrature=4, n_eq=4), -2),          # D2Q9 is degree 5 < N + 2
     (dict(quadrature=3, precision=2), -2),     # 16-bit storage only for the product sets

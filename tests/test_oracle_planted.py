@@ -6,7 +6,7 @@ Planted mistakes: 1 sign of the force term; 2 no rho g dt/2 in the momentum; 3 f
 relaxed with omega instead of omega tau; 4 Lax-Wendroff streaming against xi; 5 the
 highest Hermite order dropped from the equilibrium; 6 sigma_xy without (1 - omega/2);
 7 the first-order scheme of Eq. slb relaxing with the second-order omega; 8 the driven
-DVM pushed by -g.
+DVM pushed by -g; 9 second-order upwind streaming from the downstream side.
 """
 import numpy as np
 import pytest
@@ -95,8 +95,18 @@ def _p_m2():
     return abs((a - 1j * b) / amp / linear.dvm_forced_response(g, w, kn, phi) - 1) < 3e-3
 
 
+def _p_n2():
+    """Second-order upwind history equals the linear-mode propagation with its symbol."""
+    P = oracle.Problem("D2Q16-GH", 2, 32, 1, 0.1, streaming="upwind2")
+    f = P.init_shear(1e-6)
+    d = P.run(f, 100)
+    A, S = linear.lb_linear_history(P.vs.xi, P.vs.w, P.omega, P.dx, P.dt, 1e-6, 100, streaming="upwind2")
+    return bool(np.max(np.abs(d[:, 4] - A)) < 1e-5 * np.max(np.abs(A)) and
+                np.max(np.abs(d[:, 5] - S)) < 1e-5 * np.max(np.abs(S)))
+
+
 PINS = {"P-c": _p_c, "P-e": _p_e, "P-j1": _p_j1, "P-j2": _p_j2, "P-j3": _p_j3, "P-k1": _p_k1, "P-l1": _p_l1,
-        "P-m2": _p_m2}
+        "P-m2": _p_m2, "P-n2": _p_n2}
 
 
 def test_all_pins_hold_for_the_oracle():
@@ -112,6 +122,7 @@ def test_all_pins_hold_for_the_oracle():
     (6, {"P-e"}),
     (7, {"P-l1"}),
     (8, {"P-m2"}),
+    (9, {"P-n2"}),
 ])
 def test_planted_mistake_is_caught(plant, expect_failing):
     with oracle.planted(plant):
