@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from lbtest import f32_tol, f64_tol, lib, order_map, rel_l2
+from lbtest import f32_tol, f64_tol, lib, oracle_from_fields, order_map, random_fields, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -48,14 +48,21 @@ def test_upwind_f32_moments(quad, N):
     assert np.linalg.norm(m["sxy"] - o["sxy"]) / np.linalg.norm(o["uy"]) < f32_tol(20)
 
 
-@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 2, 1), ("D2Q16-GH", 2, 6, 3), ("D2Q64-GH", 4, 33, 2),
-                                          ("D2Q36-GH", 2, 64, 1)])
+@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 2, 1), ("D2Q16-GH", 2, 6, 3), ("D2Q64-GH", 4, 34, 2),
+                                          ("D2Q36-GH", 2, 64, 1), ("D2Q16-GH", 3, 98, 5)])
 def test_upwind_f64_edge_shapes(quad, N, nx, ny):
+    """Tiny, ragged and degenerate grids from random smooth fields (all modes present)."""
+    Lattice, capi = lib()
     steps = 12
-    L, P, f, d, capi = pair(quad, N, nx, ny, 0.3, "f64", steps)
+    rho, ux, uy, T = random_fields(nx, ny, seed=nx * 131 + ny)
+    L = Lattice(quad, N, nx, ny, 0.2, precision="f64", streaming="upwind2").init_fields(rho, ux, uy, T)
+    P = oracle.Problem(quad, N, nx, ny, 0.2, streaming="upwind2")
+    f = oracle_from_fields(P, rho, ux, uy, T)
+    L.step(steps)
+    P.run(f, steps, record=False)
     perm = order_map(capi, quad, P)
     w = P.vs.w[perm][:, None, None]
-    assert rel_l2(L.populations() - w, f[perm] - w) < f64_tol(steps, 1e-2)
+    assert rel_l2(L.populations() - w, f[perm] - w) < f64_tol(steps, 2e-2)
 
 
 def test_upwind_forced_f64_matches_oracle():
