@@ -200,6 +200,15 @@ lb_status lb_populations(lb_handle *h, double *f);
  * oldest first, into out; *n_out receives the count.  Synchronises. */
 lb_status lb_diagnostics(lb_handle *h, lb_diag *out, int max_records, int *n_out);
 
+/* The record of one time level, without waiting for the levels enqueued after it: waits
+ * only until the launch that produced `level` has completed (later levels keep running on
+ * the handle's stream), then copies its record into *out (caller host memory) on a stream
+ * of the handle's own.  So a loop that enqueues level n + 1 before reading level n keeps
+ * the GPU busy.  level in [max(0, current - diag_capacity + 1), current].
+ * Errors: LB_ERR_ARG (level outside the ring), LB_ERR_STATE (no init yet), LB_ERR_CUDA,
+ * LB_ERR_UNSTABLE (the record's sums are non-finite; *out is written). */
+lb_status lb_diagnostics_at(lb_handle *h, long long level, lb_diag *out);
+
 /* Decay rate of the shear-wave amplitude (FP64, host): minus the least-squares
  * slope of ln|A(n)| against t over the diagnostics records with t >= t_start,
  * up to the first record whose |A| falls below floor_rel * |A(0)|.  Needs the

@@ -125,6 +125,7 @@ def _load() -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.c_void_p]),
         "lb_populations": (ctypes.c_int, [H, dp]),
         "lb_diagnostics": (ctypes.c_int, [H, ctypes.POINTER(lb_diag), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "lb_diagnostics_at": (ctypes.c_int, [H, ctypes.c_longlong, ctypes.POINTER(lb_diag)]),
         "lb_synchronize": (ctypes.c_int, [H]),
         "lb_get_info": (ctypes.c_int, [H, ctypes.POINTER(lb_info_t)]),
         "lb_kernel_launches": (ctypes.c_longlong, [H]),
@@ -188,7 +189,7 @@ EXPORTS = [
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
     "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static", "lb_dvm_run",
-    "lb_dvm_run_forced",
+    "lb_dvm_run_forced", "lb_diagnostics_at",
 ]
 
 
@@ -265,6 +266,13 @@ def lb_diagnostics(h, max_records: int):
     check(lib.lb_diagnostics(h, out, max_records, ctypes.byref(n)), h)
     arr = np.frombuffer(out, dtype=DIAG_DTYPE, count=n.value).copy()
     return arr
+
+
+def lb_diagnostics_at(h, level: int, out: lb_diag | None = None) -> lb_diag:
+    """Record of one level, waiting only for the launch that produced it."""
+    out = out if out is not None else lb_diag()
+    check(lib.lb_diagnostics_at(h, level, ctypes.byref(out)), h)
+    return out
 
 
 def lb_synchronize(h):

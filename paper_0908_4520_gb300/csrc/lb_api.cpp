@@ -127,8 +127,27 @@ struct lb_handle {
     double* pop = nullptr;   // q * ncell scratch for lb_populations
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t pair[2] = {nullptr, nullptr};
+    // completion markers of the enqueued levels: ev[i] follows the launch that produced
+    // level ev_level[i] (lb_diagnostics_at waits on the first marker at or past a level)
+    static constexpr int kMarks = 8;
+    cudaEvent_t ev[kMarks] = {};
+    long long ev_level[kMarks] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int ev_next = 0;
+    cudaStream_t copy_stream = nullptr;  // record read-back beside the running levels
     std::vector<std::pair<void*, size_t>> allocs;
     std::string err;
+
+    lb_status mark_level() {
+        if (!ev[ev_next]) {
+            const cudaError_t e = cudaEventCreateWithFlags(&ev[ev_next], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        }
+        const cudaError_t e = cudaEventRecord(ev[ev_next], stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        ev_level[ev_next] = level;
+        ev_next = (ev_next + 1) % kMarks;
+        return LB_OK;
+    }
 
     lb_status fail(lb_status s, const std::string& m) {
         err = m;
@@ -152,6 +171,13 @@ struct lb_handle {
         return ptr;
     }
     void release() {
+        for (int i = 0; i < kMarks; ++i) {
+            if (ev[i]) cudaEventDestroy(ev[i]);
+            ev[i] = nullptr;
+            ev_level[i] = -1;
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+        copy_stream = nullptr;
         for (int i = 0; i < 2; ++i) {
             if (chunk[i]) cudaGraphExecDestroy(chunk[i]);
             if (pair[i]) cudaGraphExecDestroy(pair[i]);
@@ -349,7 +375,8 @@ lb_status init_common(lb_handle* h, double u0, double u1, const double* d_rho, c
     h->raw_prev = true;
     h->level = 0;
     h->initialized = true;
-    return LB_OK;
+    for (long long& l : h->ev_level) l = -1;  // markers of the previous run are stale
+    return h->mark_level();
 }
 
 }  // namespace
@@ -683,6 +710,7 @@ lb_status lb_step(lb_handle* h, int n) {
         h->level += len;
         h->raw_prev = false;
         n -= len;
+        if (n == 0) return h->mark_level();
     }
     return LB_OK;
 }
@@ -764,6 +792,29 @@ lb_status lb_diagnostics(lb_handle* h, lb_diag* out, int max_records, int* n_out
     }
     *n_out = (int)cnt;
     return st;
+}
+
+lb_status lb_diagnostics_at(lb_handle* h, long long level, lb_diag* out) {
+    if (!h || !out) return h ? h->fail(LB_ERR_ARG, "null output") : LB_ERR_ARG;
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_diagnostics_at before an init call");
+    const long long cap = h->p.diag_capacity;
+    if (level < 0 || level > h->level || level <= h->level - cap)
+        return h->fail(LB_ERR_ARG, "level not in the diagnostics ring");
+    // the first completion marker at or past the level (a later one is also sufficient)
+    int best = -1;
+    for (int i = 0; i < lb_handle::kMarks; ++i)
+        if (h->ev_level[i] >= level && (best < 0 || h->ev_level[i] < h->ev_level[best])) best = i;
+    cudaError_t e = best >= 0 ? cudaEventSynchronize(h->ev[best]) : cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "waiting for the level");
+    // the copy runs on a stream of its own, so it does not wait for the levels still
+    // running on the handle's stream
+    if (!h->copy_stream && (e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return h->cuda_fail(e, "cudaStreamCreate");
+    e = cudaMemcpyAsync(out, h->ring + level % cap, sizeof(lb_diag), cudaMemcpyDeviceToHost, h->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "diagnostics read-back");
+    if (out->flags != 0.0) return h->fail(LB_ERR_UNSTABLE, "non-finite diagnostics record");
+    return LB_OK;
 }
 
 lb_status lb_fit_decay(lb_handle* h, double t_start, double floor_rel, double* rate, int* npoints,

@@ -408,6 +408,9 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_MINB
 #define LB_TMA_MINB 1
 #endif
+#ifndef LB_DIAG_PREFETCH
+#define LB_DIAG_PREFETCH 1  // load sin/cos of the diagnostics before the collision
+#endif
 
 // cells per lane along x (FP64 storage: always 1)
 template <class VS, class S, int OVERRIDE>
@@ -936,6 +939,19 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     // compiled out of the unforced step kernels
     constexpr bool STEP = (KIND == kStep || KIND == kStepForced);
     const bool forced = (KIND != kStep) && A.force_amp != 0.0;
+    // sin(x_i), cos(x_i) of the diagnostics, loaded before the collision so that their
+    // latency hides behind it (index clamped: lanes that own no cell add nothing)
+    R dsin[V], dcos[V];
+    if constexpr (STEP && LB_DIAG_PREFETCH) {
+        if (diag) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int xi = min(max(g.x + k, 0), A.nx - 1);
+                dsin[k] = __ldg(A.sinx + xi);
+                dcos[k] = __ldg(A.cosx + xi);
+            }
+        }
+    }
     T gf = vsplat<T>(R(0));
     if (forced) {
         R gl[V];
@@ -1033,8 +1049,12 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
                 acc[0] += lane_get<k>(co.drho);
                 acc[1] += lane_get<k>(co.jx);
                 acc[2] += lane_get<k>(co.jy);
-                acc[3] = fma(lane_get<k>(co.uy), A.sinx[g.x + k], acc[3]);
-                acc[4] = fma(lane_get<k>(co.sig), A.cosx[g.x + k], acc[4]);
+                if constexpr (!LB_DIAG_PREFETCH) {
+                    dsin[k] = A.sinx[g.x + k];
+                    dcos[k] = A.cosx[g.x + k];
+                }
+                acc[3] = fma(lane_get<k>(co.uy), dsin[k], acc[3]);
+                acc[4] = fma(lane_get<k>(co.sig), dcos[k], acc[4]);
                 acc[5] += lane_get<k>(co.h);
             });
         }

@@ -86,6 +86,8 @@ def test_null_handle_calls(capi):
     assert capi.lib.lb_destroy(None) == 0
     assert capi.lib.lb_step(None, 1) == -1
     assert capi.lib.lb_synchronize(None) == -1
+    rec = capi.lb_diag()
+    assert capi.lib.lb_diagnostics_at(None, 0, ctypes.byref(rec)) == -1
 
 
 @pytest.mark.parametrize("name", oq.names())

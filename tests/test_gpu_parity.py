@@ -226,3 +226,26 @@ def test_full_size_conservation():
     assert np.max(np.abs(rec["mom_y"])) < 1e-3
     assert np.all(rec["flags"] == 0)
     L.close()
+
+
+def test_diagnostics_at_reads_each_level_while_the_next_runs():
+    """lb_diagnostics_at(n) equals the ring's record of level n, read while later levels run."""
+    Lattice, capi = lib()
+    L = Lattice("D2Q36-GH", 3, 4096, 64, 0.1, diag_capacity=64).init_shear_wave(1e-3, 1e-3)
+    recs = [capi.lb_diagnostics_at(L.h, 0)]
+    for n in range(1, 41):
+        L.step(1)
+        recs.append(capi.lb_diagnostics_at(L.h, n - 1))
+    L.step(33)  # a graph chunk plus a single level, markers only at the end of the call
+    ref = L.diagnostics()
+    got = np.array([(r.t, r.amp, r.shear, r.mass) for r in recs[1:]] +
+                   [tuple(getattr(capi.lb_diagnostics_at(L.h, n), k) for k in ("t", "amp", "shear", "mass"))
+                    for n in range(40, 74)])
+    want = np.array([(r["t"], r["amp"], r["shear"], r["mass"]) for r in ref])
+    assert len(got) == 74 and len(want) == 64
+    np.testing.assert_array_equal(got[10:], want)  # the ring keeps the last 64 of 74 levels
+    with pytest.raises(capi.LBError) as e:
+        capi.lb_diagnostics_at(L.h, 5)  # overwritten
+    assert e.value.status == capi.LB_ERR_ARG
+    with pytest.raises(capi.LBError):
+        capi.lb_diagnostics_at(L.h, 75)  # not produced yet
