@@ -408,8 +408,21 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_MINB
 #define LB_TMA_MINB 1
 #endif
+#ifndef LB_TMA_BAND
+// TMA kernel tile order: -1 per set, 0 row-major, B > 0 column-major in bands of B tile rows.
+// Measured at 4096^2 FP32 (same box; row-major / bands of 4, 8, 16): D2Q37 12.6 / 18.2 / 16.7 /
+// 14.6 GLUPS, D2Q36-GH 14.8 / 7.7 / 7.6 / 7.4, D2Q16-GH 38.5 / 35.3 / 32.4 / 31.2, D2Q36-GH FP16
+// 16.8 / 15.6 / 11.8 / 14.8: bands for the exact-shift sets, row-major for Lax-Wendroff
+#define LB_TMA_BAND -1
+#endif
+#ifndef LB_TMA_BAND_SHIFT
+#define LB_TMA_BAND_SHIFT 4  // band height of the exact-shift sets under LB_TMA_BAND = -1
+#endif
 #ifndef LB_DIAG_PREFETCH
-#define LB_DIAG_PREFETCH 1  // load sin/cos of the diagnostics before the collision
+// load sin/cos of the diagnostics before the collision: -1 per set (measured at 4096^2 FP32,
+// TMA kernel, same box: D2Q16-GH 35.7 -> 38.5 GLUPS, D2Q37 12.6 -> 12.6, D2Q36-GH
+// 14.8 -> 11.8, so only D2Q16-GH), 0 never, 1 always
+#define LB_DIAG_PREFETCH -1
 #endif
 
 // cells per lane along x (FP64 storage: always 1)
@@ -443,6 +456,7 @@ struct TmaCfg {
     static constexpr bool TILE_SYNC =
         LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && HALO && sizeof(S) == 4 && VS::Q == 36);
     static constexpr int TWO = HALO ? 30 : TW;           // cells a tile row produces
+    static constexpr int BAND = LB_TMA_BAND >= 0 ? LB_TMA_BAND : (LW ? 0 : LB_TMA_BAND_SHIFT);  // tile order
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
     static constexpr int BW = HALO ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
     static constexpr int BH = LW ? ROWS + 2 : ROWS;
@@ -532,6 +546,26 @@ __device__ __forceinline__ Lane halo_lane_geometry(int lane, int x0, int tile_st
     g.own = lane >= 1 && lane <= 30 && g.x < nx && g.x >= tile_start;
     g.xl = g.x;
     return g;
+}
+
+// Tile (ty, tx) of the TMA kernel's tile index.  Row-major (B = 0), or column-major within
+// bands of B tile rows, so that the tiles in flight at one time (consecutive indices) are
+// neighbours in x and in y: the exact-shift sets' boxes, displaced by up to max|e| rows
+// and columns, then find the rows of the tiles above and beside them in L2.
+template <int B>
+__device__ __forceinline__ void tma_tile_coords(int tile, int ntiles_x, int ntiles, int& ty, int& tx) {
+    if constexpr (B <= 0) {
+        ty = tile / ntiles_x;
+        tx = tile - ty * ntiles_x;
+    } else {
+        const int per_band = B * ntiles_x;
+        const int band = tile / per_band;
+        const int r = tile - band * per_band;
+        const int ntiles_y = ntiles / ntiles_x;
+        const int rows = min(B, ntiles_y - band * B);
+        tx = r / rows;
+        ty = band * B + (r - tx * rows);
+    }
 }
 
 template <int V>
@@ -941,8 +975,9 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     const bool forced = (KIND != kStep) && A.force_amp != 0.0;
     // sin(x_i), cos(x_i) of the diagnostics, loaded before the collision so that their
     // latency hides behind it (index clamped: lanes that own no cell add nothing)
+    constexpr bool PF = LB_DIAG_PREFETCH > 0 || (LB_DIAG_PREFETCH < 0 && !VS::kOnLattice && VS::Q == 16);
     R dsin[V], dcos[V];
-    if constexpr (STEP && LB_DIAG_PREFETCH) {
+    if constexpr (STEP && PF) {
         if (diag) {
 #pragma unroll
             for (int k = 0; k < V; ++k) {
@@ -1049,7 +1084,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
                 acc[0] += lane_get<k>(co.drho);
                 acc[1] += lane_get<k>(co.jx);
                 acc[2] += lane_get<k>(co.jy);
-                if constexpr (!LB_DIAG_PREFETCH) {
+                if constexpr (!PF) {
                     dsin[k] = A.sinx[g.x + k];
                     dcos[k] = A.cosx[g.x + k];
                 }
@@ -1406,8 +1441,8 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
         if (lane == 0) {
             uint32_t it = 0;
             for (int tile = blockIdx.x; tile < A.ntiles && !*abort_flag; tile += gridDim.x) {
-                const int ty = tile / A.ntiles_x;
-                const int tx = tile - ty * A.ntiles_x;
+                int ty, tx;
+                tma_tile_coords<C::BAND>(tile, A.ntiles_x, A.ntiles, ty, tx);
                 const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tx * C::TWO;
                 const int y0 = ty * ROWS;
                 for (int grp = 0; grp < NG; ++grp, ++it) {
@@ -1448,8 +1483,8 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
         int st_i = 0;
         uint32_t st_ph = 0;
         for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
-            const int ty = tile / A.ntiles_x;
-            const int tx = tile - ty * A.ntiles_x;
+            int ty, tx;
+            tma_tile_coords<C::BAND>(tile, A.ntiles_x, A.ntiles, ty, tx);
             const int tile_start = tx * C::TWO;
             const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
             const int y = ty * ROWS + warp;
