@@ -127,6 +127,7 @@ struct lb_handle {
     double* pop = nullptr;   // q * ncell scratch for lb_populations
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t pair[2] = {nullptr, nullptr};
+    cudaGraphExec_t single[2] = {nullptr, nullptr};  // one level (parameters uploaded once)
     // completion markers of the enqueued levels: ev[i] follows the launch that produced
     // level ev_level[i] (lb_diagnostics_at waits on the first marker at or past a level)
     static constexpr int kMarks = 8;
@@ -181,7 +182,8 @@ struct lb_handle {
         for (int i = 0; i < 2; ++i) {
             if (chunk[i]) cudaGraphExecDestroy(chunk[i]);
             if (pair[i]) cudaGraphExecDestroy(pair[i]);
-            chunk[i] = pair[i] = nullptr;
+            if (single[i]) cudaGraphExecDestroy(single[i]);
+            chunk[i] = pair[i] = single[i] = nullptr;
         }
         if (stream) cudaStreamSynchronize(stream);
         for (auto& a : allocs) {
@@ -353,7 +355,8 @@ lb_status set_scale_and_tables(lb_handle* h, double amp) {
     for (int i = 0; i < 2; ++i) {
         if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
         if (h->pair[i]) cudaGraphExecDestroy(h->pair[i]);
-        h->chunk[i] = h->pair[i] = nullptr;
+        if (h->single[i]) cudaGraphExecDestroy(h->single[i]);
+        h->chunk[i] = h->pair[i] = h->single[i] = nullptr;
     }
     return LB_OK;
 }
@@ -687,6 +690,8 @@ lb_status lb_step(lb_handle* h, int n) {
     if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_step before an init call");
     lb_status st;
     while (n > 0) {
+        // graphs of 32, 2 or 1 levels, one per buffer parity, built on first use: a replay
+        // costs one launch call and no parameter upload
         cudaGraphExec_t* g = nullptr;
         int len = 0;
         if (n >= kChunk) {
@@ -695,17 +700,15 @@ lb_status lb_step(lb_handle* h, int n) {
         } else if (n >= 2) {
             g = &h->pair[h->cur];
             len = 2;
-        }
-        if (g) {
-            if (!*g && (st = build_graph(h, h->cur, len, g)) != LB_OK) return st;
-            const cudaError_t e = cudaGraphLaunch(*g, h->stream);
-            if (e != cudaSuccess) return h->cuda_fail(e, "cudaGraphLaunch");
-            h->launches += len;
         } else {
+            g = &h->single[h->cur];
             len = 1;
-            if ((st = step_once(h, h->cur)) != LB_OK) return st;
         }
-        // len is even for graphs: cur returns to itself; odd single step flips it
+        if (!*g && (st = build_graph(h, h->cur, len, g)) != LB_OK) return st;
+        const cudaError_t e = cudaGraphLaunch(*g, h->stream);
+        if (e != cudaSuccess) return h->cuda_fail(e, "cudaGraphLaunch");
+        h->launches += len;
+        // an even number of levels returns cur to itself; an odd one flips it
         if (len & 1) h->cur = 1 - h->cur;
         h->level += len;
         h->raw_prev = false;

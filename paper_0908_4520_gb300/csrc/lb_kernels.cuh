@@ -365,8 +365,8 @@ struct Pack<float, 2> {
 // Launch shapes, from sweeps at 4096^2 (FP32, N = 3) and 2048^2 (D2Q64, N = 4):
 //  * Lax-Wendroff (Gauss-Hermite product) sets: one cell per lane and many warps
 //    (19 consumer rows, or 15 for q = 64), 6 velocities per TMA stage (12 for q = 64);
-//  * exact-shift sets: two cells per lane (packed f32x2), 11 consumer rows, 18
-//    velocities per stage.
+//  * exact-shift sets: two cells per lane (packed f32x2), 11 consumer rows (13 for
+//    q <= 25), 18 velocities per stage.
 // The plain-load kernel takes the same cells per lane as the TMA-staged one, so the
 // two give the same bits.  Each value is overridable at build time (0 = the choice above).
 #ifndef LB_CFG_V
@@ -445,7 +445,9 @@ struct TmaCfg {
     static constexpr bool LW = !VS::kOnLattice;
     static constexpr int V = cells_per_lane<VS, S, LB_TMA_V>();
     // consumer warps (+ one producer warp); the register cap follows from the count
-    static constexpr int ROWS = LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : 11);
+    // (exact shift at 4096^2 FP32, 11 / 13 rows, GLUPS: D2Q37 18.3 / 16.8, D2Q25 21.3 / 22.3,
+    // D2Q21 25.4 / 27.7, D2Q17 41.6 / 42.1, D2Q16 44.7 / 45.1, D2Q9 68.6 / 72.6)
+    static constexpr int ROWS = LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : (VS::Q > 30 ? 11 : 13));
     static constexpr int TW = 32 * V;
     // Edge lanes as halo lanes (30 cells a row) and a per-tile barrier of the consumer warps,
     // chosen per set and storage by the sweep at 4096^2 / 2048^2 (GLUPS, no halo / halo /
