@@ -97,7 +97,8 @@ typedef enum { LB_SCHEME_SECOND_ORDER = 0, LB_SCHEME_FIRST_ORDER = 1 } lb_scheme
  *   its two upstream neighbours: out_i = f_i - c/2 (3 f_i - 4 f_{i-s} + f_{i-2s})
  *   + c^2/2 (f_i - 2 f_{i-s} + f_{i-2s}), c = |C|, s = sign(C), C = xi dt/dx
  *   (exact shift at c = 1).  Off-lattice sets with F32/F64 storage only
- *   (LB_ERR_UNSUPPORTED otherwise); steps run the plain-load kernel. */
+ *   (LB_ERR_UNSUPPORTED otherwise); the rim holds two ghost rows.  F32 steps run the
+ *   TMA-staged kernel (28-cell tile rows), F64 the plain-load kernel; same bits. */
 typedef enum { LB_STREAM_LAX_WENDROFF = 0, LB_STREAM_UPWIND2 = 1 } lb_streaming;
 
 typedef struct {

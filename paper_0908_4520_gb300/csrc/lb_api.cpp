@@ -480,8 +480,6 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     const bool upwind = P.streaming == LB_STREAM_UPWIND2;
     if (upwind && (P.precision == LB_BF16 || P.precision == LB_F16))
         return reject(LB_ERR_UNSUPPORTED, "second-order upwind streaming is built for F32/F64 storage");
-    if (upwind && P.step_kernel == 2)
-        return reject(LB_ERR_UNSUPPORTED, "second-order upwind streaming runs the plain-load kernel");
     if (!(P.kn > 0) || !std::isfinite(P.kn)) return reject(LB_ERR_ARG, "kn must be positive");
     if (!(P.cfl > 0 && P.cfl <= 1.0)) return reject(LB_ERR_ARG, "cfl must be in (0, 1]");
     if (P.diag_capacity < 1) return reject(LB_ERR_ARG, "diag_capacity must be >= 1");
@@ -542,6 +540,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         lbk::Launch L{};
         L.kind = lbk::kQueryShape;
         L.n_eq = P.n_eq;
+        L.upwind = upwind;  // the TMA-staged kernel (and box) of this streaming
         L.args = &h->shape;
         if (h->launch(L) != cudaSuccess) {
             h->shape.V = 1;
@@ -582,7 +581,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         delete h;
         return reject(LB_ERR_UNSUPPORTED, "the TMA-staged step kernel runs the free wave; forced runs use the plain kernel");
     }
-    if (h->shape.tma && P.force_amp == 0.0 && !upwind) {
+    if (h->shape.tma && P.force_amp == 0.0) {
         const int ttw = h->shape.tma_tw;
         h->tma_ntiles_x = (P.nx + ttw - 1) / ttw;
         h->tma_x0_last = P.nx >= ttw ? P.nx - ttw : 0;

@@ -440,10 +440,14 @@ struct Cfg {
     static constexpr int MINB = LB_CFG_MINB > 0 ? LB_CFG_MINB : (V == 1 && sizeof(S) != 8 ? 2 : 1);
 };
 
-template <class VS, class S>
+// UPW: second-order upwind streaming of a Lax-Wendroff set (one cell per lane): lanes
+// 0, 1 and 30, 31 compute the y pass of the two columns on either side of the 28 cells
+// that lanes 2..29 own, and the box carries two extra rows above and below.
+template <class VS, class S, bool UPW = false>
 struct TmaCfg {
     static constexpr bool LW = !VS::kOnLattice;
     static constexpr int V = cells_per_lane<VS, S, LB_TMA_V>();
+    static_assert(!UPW || (LW && V == 1), "upwind TMA staging: Lax-Wendroff sets, one cell per lane");
     // consumer warps (+ one producer warp); the register cap follows from the count
     // (exact shift at 4096^2 FP32, 11 / 13 rows, GLUPS: D2Q37 18.3 / 16.8, D2Q25 21.3 / 22.3,
     // D2Q21 25.4 / 27.7, D2Q17 41.6 / 42.1, D2Q16 44.7 / 45.1, D2Q9 68.6 / 72.6)
@@ -454,14 +458,15 @@ struct TmaCfg {
     // halo + barrier): D2Q16 FP32 29.5 / 35.5 / 30.4; D2Q36 FP32 12.5 / 9.6 / 14.5; D2Q36
     // 16-bit 12.1 / 15.9 / 14.4; D2Q64 FP32 5.38 / 4.95 / 4.97; D2Q64 16-bit 4.37 / 6.40 / 6.28.
     static constexpr bool FP32_Q64 = sizeof(S) == 4 && VS::Q > 40;
-    static constexpr bool HALO = LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64));
+    static constexpr bool HALO = !UPW && LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64));
     static constexpr bool TILE_SYNC =
-        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && HALO && sizeof(S) == 4 && VS::Q == 36);
-    static constexpr int TWO = HALO ? 30 : TW;           // cells a tile row produces
+        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && (HALO || UPW) && sizeof(S) == 4 && VS::Q == 36);
+    static constexpr int TWO = UPW ? 28 : (HALO ? 30 : TW);  // cells a tile row produces
+    static constexpr int GX = UPW ? 2 : 1;              // stencil reach (columns and rows) of the box
     static constexpr int BAND = LB_TMA_BAND >= 0 ? LB_TMA_BAND : (LW ? 0 : LB_TMA_BAND_SHIFT);  // tile order
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
-    static constexpr int BW = HALO ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
-    static constexpr int BH = LW ? ROWS + 2 : ROWS;
+    static constexpr int BW = (HALO || UPW) ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
+    static constexpr int BH = LW ? ROWS + 2 * GX : ROWS;
     static constexpr int BOX = BW * BH;                 // elements of one velocity's box
     // stride of the velocity slots in a stage: dense for one 3-D box (Lax-Wendroff),
     // 128-byte aligned for separate boxes (exact shift)
@@ -546,6 +551,16 @@ __device__ __forceinline__ Lane halo_lane_geometry(int lane, int x0, int tile_st
     Lane g;
     g.x = x0 - 1 + lane;
     g.own = lane >= 1 && lane <= 30 && g.x < nx && g.x >= tile_start;
+    g.xl = g.x;
+    return g;
+}
+
+// The same for second-order upwind: lanes 0, 1 and 30, 31 are halo lanes (columns
+// x0 - 2, x0 - 1, x0 + 28, x0 + 29); lanes 2..29 own cells x0 .. x0 + 27.
+__device__ __forceinline__ Lane upwind_lane_geometry(int lane, int x0, int tile_start, int nx) {
+    Lane g;
+    g.x = x0 - 2 + lane;
+    g.own = lane >= 2 && lane <= 29 && g.x < nx && g.x >= tile_start;
     g.xl = g.x;
     return g;
 }
@@ -1405,11 +1420,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
     }
 }
 
-template <class VS, int N, class S>
-__global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
+template <class VS, int N, class S, bool UPW = false>
+__global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
     lb_tma_step_kernel(const __grid_constant__ Args<float> A) {
     using R = float;
-    using C = TmaCfg<VS, S>;
+    using C = TmaCfg<VS, S, UPW>;
     constexpr int Q = VS::Q, V = C::V, ROWS = C::ROWS, TW = C::TW, AL = C::AL;
     constexpr int NS = C::NS, NG = C::NG, K = C::K, BW = C::BW, BOX = C::BOX, SLOT = C::SLOT;
     constexpr int STAGE_ELEMS = C::STAGE_BYTES / (int)sizeof(S);
@@ -1461,8 +1476,8 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                     S* dstage = stages + (long long)s * STAGE_ELEMS;
                     if constexpr (C::LW) {
                         mbar_arrive_expect_tx(&full[s], (uint32_t)(K * BOX * sizeof(S)));
-                        const int xs = ((x0 - 1 + kGhostX) / AL) * AL;
-                        tma_load_3d(dstage, &A.tmap, &full[s], xs, y0 - 1 + A.gy, a0);
+                        const int xs = ((x0 - C::GX + kGhostX) / AL) * AL;
+                        tma_load_3d(dstage, &A.tmap, &full[s], xs, y0 - C::GX + A.gy, a0);
                     } else {
                         mbar_arrive_expect_tx(&full[s], (uint32_t)(na * BOX * sizeof(S)));
                         for (int j = 0; j < na; ++j) {
@@ -1490,8 +1505,9 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
             const int tile_start = tx * C::TWO;
             const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
             const int y = ty * ROWS + warp;
-            const Lane g = C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx)
-                                   : lane_geometry<V>(lane, x0, tile_start, A.nx);
+            const Lane g = UPW      ? upwind_lane_geometry(lane, x0, tile_start, A.nx)
+                           : C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx)
+                                     : lane_geometry<V>(lane, x0, tile_start, A.nx);
             using T = typename Pack<R, V>::T;
             T ft[Q];
             bool ok = !*abort_flag;
@@ -1514,7 +1530,32 @@ __global__ void __maxnreg__((TmaCfg<VS, S>::MAXREG))
                         if constexpr (a < Q) {
                             const R sc = load_scale<S, R>(A.tab, a);
                             const S* box = st + j * SLOT;
-                            if constexpr (C::LW) {
+                            if constexpr (UPW) {
+                                // second-order upwind: y pass over the lane's column in the cell's
+                                // row and its two upstream rows (box row of row y: warp + 2), x pass
+                                // from the two upstream lanes (the same operation order as the
+                                // plain-load kernel, so the two give the same bits)
+                                const R one = R(1);
+                                constexpr int ix = VS::ix(a), iy = VS::iy(a);
+                                constexpr int sx = VS::axis_sign(ix), sy = VS::axis_sign(iy);
+                                const R yf = A.tab.uw[iy][0], yn = A.tab.uw[iy][1], ys = A.tab.uw[iy][2];
+                                const R xf = A.tab.uw[ix][0], xn = A.tab.uw[ix][1], xs = A.tab.uw[ix][2];
+                                const int c = ((x0 - 2 + kGhostX) & (AL - 1)) + lane;
+                                const S* r0 = box + (warp + 2) * BW;
+                                const S* rn = r0 - sy * BW;
+                                const S* rf = r0 - 2 * sy * BW;
+                                const R gv = fma(yf, sld1<S, R>(rf + c, one),
+                                                 fma(yn, sld1<S, R>(rn + c, one), ys * sld1<S, R>(r0 + c, one)));
+                                R g1, g2;
+                                if constexpr (sx > 0) {
+                                    g1 = __shfl_up_sync(0xffffffffu, gv, 1);
+                                    g2 = __shfl_up_sync(0xffffffffu, gv, 2);
+                                } else {
+                                    g1 = __shfl_down_sync(0xffffffffu, gv, 1);
+                                    g2 = __shfl_down_sync(0xffffffffu, gv, 2);
+                                }
+                                ft[a] = fma(xf, g2, fma(xn, g1, xs * gv));
+                            } else if constexpr (C::LW) {
                                 // the stencil is linear: 16-bit values are scaled once, after it
                                 const R one = R(1);
                                 constexpr int ix = VS::ix(a), iy = VS::iy(a);
@@ -1644,6 +1685,10 @@ cudaError_t launch_typed(const Launch& L) {
     using C = Cfg<VS, S>;
     using T = TmaCfg<VS, S>;
     constexpr bool kTma = std::is_same<R, float>::value && T::NS >= 2;
+    // second-order upwind streaming: Lax-Wendroff sets with 32/64-bit storage; TMA-staged
+    // for FP32 storage
+    constexpr bool kUpw = !VS::kOnLattice && !Is16<S>::value;
+    constexpr bool kUpwTma = kUpw && kTma && std::is_same<S, float>::value;
     if (L.kind == kQueryShape) {
         Shape* sh = static_cast<Shape*>(const_cast<void*>(L.args));
         sh->V = C::V;
@@ -1653,28 +1698,41 @@ cudaError_t launch_typed(const Launch& L) {
             &sh->occupancy, lb_fused_kernel<VS, N, S, R, kStep>, C::THREADS, 0);
         if (e != cudaSuccess) return e;
         sh->tma = 0;
-        if constexpr (kTma) {
-            e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     T::SMEM);  // fixed per kernel: every handle of the unit asks the same
-            if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->tma_occupancy, lb_tma_step_kernel<VS, N, S>,
-                                                              T::THREADS, T::SMEM);
-            if (e != cudaSuccess) return e;
+        // the TMA-staged kernel of the requested streaming, and its box
+        auto tma_shape = [&](auto kernel, auto cfg) -> cudaError_t {
+            using TC = decltype(cfg);
+            cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 TC::SMEM);  // fixed per kernel: every handle asks the same
+            if (r != cudaSuccess) return r;
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->tma_occupancy, kernel, TC::THREADS, TC::SMEM);
+            if (r != cudaSuccess) return r;
             sh->tma = sh->tma_occupancy > 0 ? 1 : 0;
-            sh->tma_V = T::V;
-            sh->tma_tw = T::TWO;
-            sh->tma_rows = T::ROWS;
-            sh->tma_threads = T::THREADS;
-            sh->tma_smem = T::SMEM;
-            sh->box_w = T::BW;
-            sh->box_h = T::BH;
-            sh->box_d = T::BOX_D;
+            sh->tma_V = TC::V;
+            sh->tma_tw = TC::TWO;
+            sh->tma_rows = TC::ROWS;
+            sh->tma_threads = TC::THREADS;
+            sh->tma_smem = TC::SMEM;
+            sh->box_w = TC::BW;
+            sh->box_h = TC::BH;
+            sh->box_d = TC::BOX_D;
+            return cudaSuccess;
+        };
+        if (L.upwind) {
+            if constexpr (kUpwTma) e = tma_shape(lb_tma_step_kernel<VS, N, S, true>, TmaCfg<VS, S, true>{});
+        } else {
+            if constexpr (kTma) e = tma_shape(lb_tma_step_kernel<VS, N, S>, T{});
         }
-        return cudaSuccess;
+        return e;
     }
     const Args<R>& A = *static_cast<const Args<R>*>(L.args);
-    // second-order upwind streaming: Lax-Wendroff sets with 32/64-bit storage, register kernel
-    constexpr bool kUpw = !VS::kOnLattice && !Is16<S>::value;
+    if (L.upwind && L.kind == kStepTma) {
+        if constexpr (kUpwTma) {
+            using TU = TmaCfg<VS, S, true>;
+            lb_tma_step_kernel<VS, N, S, true><<<L.grid, TU::THREADS, TU::SMEM, L.stream>>>(A);
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
     if (L.upwind) {
         if constexpr (kUpw) {
             switch (L.kind) {

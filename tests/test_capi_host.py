@@ -66,7 +66,6 @@ def test_params_default(capi):
     (dict(streaming=2), -1),
     (dict(streaming=1, quadrature=3), -1),     # on-lattice sets stream by the exact shift
     (dict(streaming=1, precision=2), -2),      # upwind streaming: F32/F64 storage
-    (dict(streaming=1, step_kernel=2), -2),    # upwind streaming runs the plain-load kernel
     (dict(kn=0.0), -1), (dict(kn=-1.0), -1), (dict(cfl=1.5), -1), (dict(cfl=0.0), -1),
     (dict(quadrature=4, n_eq=4), -2),          # D2Q9 is degree 5 < N + 2
     (dict(quadrature=3, precision=2), -2),     # 16-bit storage only for the product sets

@@ -1,7 +1,8 @@
 """Second-order upwind streaming of the Gauss-Hermite product sets on the GPU against the
 FP64 oracle (same tolerances as the Lax-Wendroff parity tests).  Grids span several
-32-column tiles with ragged tails, and the degenerate shapes (nx = 2, ny = 1) whose
-upstream columns and rows are all periodic images."""
+tiles with ragged tails, and the degenerate shapes (nx = 2, ny = 1) whose upstream
+columns and rows are all periodic images.  FP32 storage also runs the TMA-staged kernel
+(28-cell tile rows with two halo lanes on each side), bitwise equal to the plain one."""
 import numpy as np
 import pytest
 
@@ -88,3 +89,27 @@ def test_upwind_full_size_conserves_and_differs_from_lax_wendroff():
     np.testing.assert_allclose(ra["mass"], ra["mass"][0], rtol=1e-6)
     # same physics to O(dx^2): amplitudes agree closely but not bitwise
     assert 0 < np.max(np.abs(ra["amp"] - rb["amp"])) < 1e-3 * abs(rb["amp"][0])
+
+
+@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 200, 23), ("D2Q16-GH", 2, 90, 7), ("D2Q64-GH", 4, 130, 17),
+                                          ("D2Q36-GH", 1, 58, 40)])
+def test_upwind_tma_and_plain_kernels_are_bitwise_equal(quad, N, nx, ny):
+    Lattice, capi = lib()
+    a = Lattice(quad, N, nx, ny, 0.3, streaming="upwind2", step_kernel="tma").init_shear_wave(1e-3, 1e-3)
+    b = Lattice(quad, N, nx, ny, 0.3, streaming="upwind2", step_kernel="plain").init_shear_wave(1e-3, 1e-3)
+    assert a.info["tma_staged"] == 1 and b.info["tma_staged"] == 0
+    a.step(29)
+    b.step(29)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    np.testing.assert_allclose(a.diagnostics()["amp"], b.diagnostics()["amp"], rtol=1e-6, atol=1e-15)
+
+
+def test_upwind_tma_f32_matches_oracle():
+    Lattice, capi = lib()
+    L = Lattice("D2Q36-GH", 3, 100, 11, 0.3, streaming="upwind2", step_kernel="tma").init_shear_wave(1e-3, 1e-3)
+    L.step(20)
+    P = oracle.Problem("D2Q36-GH", 3, 100, 11, 0.3, streaming="upwind2")
+    f = P.init_shear(1e-3, 1e-3)
+    P.run(f, 20, record=False)
+    m, o = L.moments(), P.moments(f, 20)
+    assert rel_l2(m["uy"], o["uy"]) < 1e-6
