@@ -241,7 +241,7 @@ lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int ra
                       double u0, double u1, const double* i_rho, const double* i_ux, const double* i_uy,
                       const double* i_T) {
     lbk::Args<R> A;
-    const bool tma = (kind == lbk::kStepTma);
+    const bool tma = (kind == lbk::kStepTma || kind == lbk::kMomentsTma);
     h->fill_args(A, tma);
     if (tma) A.tmap = h->tmap[src == h->buf[0] ? 0 : 1];
     A.src = src;
@@ -732,8 +732,11 @@ lb_status lb_synchronize(lb_handle* h) {
 lb_status lb_moments_device(lb_handle* h, double* rho, double* ux, double* uy, double* T, double* sxy) {
     if (!h) return LB_ERR_ARG;
     if (!h->initialized) return h->fail(LB_ERR_STATE, "lb_moments before an init call");
-    // the state f~(n) = stream(buffer read by the last launch)
+    // the state f~(n) = stream(buffer read by the last launch); streamed by the TMA-staged
+    // kernel when the steps are (the raw state right after init has nothing to stream)
     const int prev = 1 - h->cur;
+    if (h->use_tma && !h->raw_prev)
+        return launch_any(h, lbk::kMomentsTma, h->buf[prev], nullptr, 0, h->tma_grid, rho, ux, uy, T, sxy, nullptr);
     return launch_any(h, lbk::kMoments, h->buf[prev], nullptr, h->raw_prev ? 1 : 0, h->grid, rho, ux, uy, T, sxy,
                       nullptr);
 }
@@ -768,8 +771,10 @@ lb_status lb_populations(lb_handle* h, double* f) {
         if (!h->pop) return h->fail(LB_ERR_NOMEM, "population scratch");
     }
     const int prev = 1 - h->cur;
-    lb_status st = launch_any(h, lbk::kMoments, h->buf[prev], nullptr, h->raw_prev ? 1 : 0, h->grid, nullptr,
-                              nullptr, nullptr, nullptr, nullptr, h->pop);
+    const bool tma = h->use_tma && !h->raw_prev;
+    lb_status st = launch_any(h, tma ? lbk::kMomentsTma : lbk::kMoments, h->buf[prev], nullptr,
+                              h->raw_prev ? 1 : 0, tma ? h->tma_grid : h->grid, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, h->pop);
     if (st != LB_OK) return st;
     const cudaError_t e = cudaMemcpyAsync(f, h->pop, 8 * n, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "population read-back");

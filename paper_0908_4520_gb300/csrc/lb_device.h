@@ -38,7 +38,9 @@ struct Tab {
     R scinv[kMaxQ];           // 16-bit storage: stored = deviation / (w S)
 };
 
-enum Kind : int { kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kStepForced = 4, kQueryShape = -1 };
+enum Kind : int {
+    kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kStepForced = 4, kMomentsTma = 5, kQueryShape = -1
+};
 
 // Population layout: plane a, row y, column x at
 //   a * plane + origin + y * pitch + x,   origin = gy * pitch + kGhostX,

@@ -1420,9 +1420,12 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
     }
 }
 
-template <class VS, int N, class S, bool UPW = false>
+// KIND = kStep: one level (store f*, diagnostics, level advance); kMoments: the per-cell
+// moments (and optionally f~) of the current level, nothing stored, no level advance.
+template <class VS, int N, class S, bool UPW = false, int KIND = kStep>
 __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
     lb_tma_step_kernel(const __grid_constant__ Args<float> A) {
+    static_assert(KIND == kStep || KIND == kMoments, "TMA-staged kinds: step, moments");
     using R = float;
     using C = TmaCfg<VS, S, UPW>;
     constexpr int Q = VS::Q, V = C::V, ROWS = C::ROWS, TW = C::TW, AL = C::AL;
@@ -1449,7 +1452,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
     __syncthreads();
 
     const long long lvl = __ldcg(A.level);
-    const bool diag = (A.diag_every > 0) && (lvl % A.diag_every == 0);
+    const bool diag = KIND == kStep && (A.diag_every > 0) && (lvl % A.diag_every == 0);
     R acc[6] = {0, 0, 0, 0, 0, 0};
     volatile int* abort_flag = &s_abort;
 
@@ -1634,7 +1637,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                 }
             });
             if (ok && y < A.ny)
-                collide_store<VS, N, S, R, V, kStep>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
+                collide_store<VS, N, S, R, V, KIND>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
             if constexpr (C::TILE_SYNC) {
                 // keep the consumer warps within one tile of each other, so a stage is
                 // released (and refilled) as soon as the last of them has read it; every
@@ -1646,7 +1649,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
         }
     }
     __syncthreads();
-    finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
+    if constexpr (KIND == kStep) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
 }
 
 // ------------------------------------------------------------ init kernel
@@ -1718,17 +1721,30 @@ cudaError_t launch_typed(const Launch& L) {
             return cudaSuccess;
         };
         if (L.upwind) {
-            if constexpr (kUpwTma) e = tma_shape(lb_tma_step_kernel<VS, N, S, true>, TmaCfg<VS, S, true>{});
+            if constexpr (kUpwTma) {
+                e = tma_shape(lb_tma_step_kernel<VS, N, S, true>, TmaCfg<VS, S, true>{});
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S, true, kMoments>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TmaCfg<VS, S, true>::SMEM);
+            }
         } else {
-            if constexpr (kTma) e = tma_shape(lb_tma_step_kernel<VS, N, S>, T{});
+            if constexpr (kTma) {
+                e = tma_shape(lb_tma_step_kernel<VS, N, S>, T{});
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S, false, kMoments>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+            }
         }
         return e;
     }
     const Args<R>& A = *static_cast<const Args<R>*>(L.args);
-    if (L.upwind && L.kind == kStepTma) {
+    if (L.upwind && (L.kind == kStepTma || L.kind == kMomentsTma)) {
         if constexpr (kUpwTma) {
             using TU = TmaCfg<VS, S, true>;
-            lb_tma_step_kernel<VS, N, S, true><<<L.grid, TU::THREADS, TU::SMEM, L.stream>>>(A);
+            if (L.kind == kStepTma)
+                lb_tma_step_kernel<VS, N, S, true><<<L.grid, TU::THREADS, TU::SMEM, L.stream>>>(A);
+            else
+                lb_tma_step_kernel<VS, N, S, true, kMoments><<<L.grid, TU::THREADS, TU::SMEM, L.stream>>>(A);
             return cudaGetLastError();
         }
         return cudaErrorNotSupported;
@@ -1770,6 +1786,12 @@ cudaError_t launch_typed(const Launch& L) {
         case kStepTma:
             if constexpr (kTma) {
                 lb_tma_step_kernel<VS, N, S><<<L.grid, T::THREADS, T::SMEM, L.stream>>>(A);
+                break;
+            }
+            return cudaErrorNotSupported;
+        case kMomentsTma:
+            if constexpr (kTma) {
+                lb_tma_step_kernel<VS, N, S, false, kMoments><<<L.grid, T::THREADS, T::SMEM, L.stream>>>(A);
                 break;
             }
             return cudaErrorNotSupported;
