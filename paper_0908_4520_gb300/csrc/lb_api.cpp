@@ -343,15 +343,23 @@ lb_status build_graph(lb_handle* h, int from, int nsteps, cudaGraphExec_t* out) 
 
 constexpr int kChunk = 32;
 
+// 16-bit storage takes its scale from the initial amplitude (unless storage_scale is set)
+bool scale_from_amplitude(const lb_handle* h) {
+    return (h->p.precision == LB_BF16 || h->p.precision == LB_F16) && !(h->p.storage_scale > 0);
+}
+
 lb_status set_scale_and_tables(lb_handle* h, double amp) {
+    double scale = 1.0;
     if (h->p.precision == LB_BF16 || h->p.precision == LB_F16) {
         double s = h->p.storage_scale;
         if (s <= 0) s = std::max(2.0 * amp, 1e-6);
-        h->scale = lbh::pow2_near(s);
-    } else {
-        h->scale = 1.0;
+        scale = lbh::pow2_near(s);
     }
-    // graphs bake the tables into their kernel parameters: rebuild on change
+    // graphs bake the tables into their kernel parameters: rebuild when the scale changes
+    if (scale == h->scale && (h->chunk[0] || h->pair[0] || h->single[0] || h->chunk[1] || h->pair[1] ||
+                              h->single[1]))
+        return LB_OK;
+    h->scale = scale;
     for (int i = 0; i < 2; ++i) {
         if (h->chunk[i]) cudaGraphExecDestroy(h->chunk[i]);
         if (h->pair[i]) cudaGraphExecDestroy(h->pair[i]);
@@ -666,7 +674,8 @@ lb_status lb_init_fields(lb_handle* h, const double* rho, const double* ux, cons
     if (!h || !rho || !ux || !uy) return h ? h->fail(LB_ERR_ARG, "rho, ux, uy are required") : LB_ERR_ARG;
     const size_t n = (size_t)h->ncell;
     double amp = 0;
-    for (size_t i = 0; i < n; ++i) amp = std::max(amp, std::max(std::fabs(ux[i]), std::fabs(uy[i])));
+    if (scale_from_amplitude(h))  // a host pass over the fields: only when the scale depends on it
+        for (size_t i = 0; i < n; ++i) amp = std::max(amp, std::max(std::fabs(ux[i]), std::fabs(uy[i])));
     set_scale_and_tables(h, amp);
     if (!h->mom) {
         h->mom = static_cast<double*>(h->dalloc(sizeof(double) * 5 * n));
