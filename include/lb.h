@@ -6,11 +6,16 @@
  * high-order lattice Boltzmann models for rarefied gas flows"):
  *   moments    rho = sum f~, rho u = sum xi f~, 2 rho T = sum |xi - u|^2 f~  (Sec. 2.2)
  *   equilibrium Hermite expansion of the Maxwellian truncated at order N     (Sec. 2.1,
- *              Eqs. approxf, an, demoeq)
- *   collision  f* = f~ - omega (f~ - f^eq), omega = dt / (tau + dt/2)         (Eq. 2order)
+ *              Eqs. approxf, an, demoeq; N = 1: Sec. 3.3, Eq. lbm1)
+ *   collision  f* = f~ - omega (f~ - f^eq), omega = dt / (tau + dt/2)         (Eq. 2order;
+ *              the first-order scheme of Eq. slb as an option)
  *   streaming  exact shift along integer e_alpha for on-lattice sets (Table 1),
  *              Lax-Wendroff for off-lattice Gauss-Hermite product sets
- *              (Sec. 2.3; Sec. 3.3; caption of the D2Q400 figure)
+ *              (Sec. 2.3; Sec. 3.3; caption of the D2Q400 figure), second-order
+ *              upwind as an option
+ * plus the body force of the driven standing shear wave (Secs. 2.1, 2.2, 4), batches
+ * of many small lattices, a request loop, and the reduced discrete velocity method of
+ * Sec. 3.3 (free and driven).
  *
  * Conventions (every function):
  *  - Returns lb_status; nothing is thrown across the ABI.  Out-pointers are
