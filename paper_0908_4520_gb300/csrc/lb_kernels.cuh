@@ -3,13 +3,15 @@
 //
 // One launch advances every cell by one time level of Eq. 2order:
 //   pull-stream   f~_a(x) = S_a[f*_a](x)        exact shift by e_a (on-lattice) or
-//                                               tensor-product Lax-Wendroff (off-lattice)
+//                                               tensor-product Lax-Wendroff (off-lattice;
+//                                               second-order upwind as an option)
 //   moments       rho, rho u, 2 rho T (Sec. 2.2, D = 2)
 //   equilibrium   f^eq_a = w_a rho sum_{kx+ky<=N} c_kx(u_x) c_ky(u_y) He_kx He_ky / (kx! ky!)
 //                 (Sec. 2.1: the Hermite coefficients of the Maxwellian factorise per
 //                 axis, c_k(u, T) = E[He_k(X)], X ~ Normal(u, T), from the recurrence
 //                 c_{k+1} = u c_k + k (T - 1) c_{k-1})
 //   relax         f*_a = f~_a + omega (f^eq_a - f~_a), omega = dt / (tau + dt/2)
+//                 (dt / tau for the first-order scheme of Eq. slb)
 //   store         f*_a (the next launch streams it)
 //   diagnostics   FP64 grid sums of the observables of f~ (mass, momentum, the
 //                 sin/cos Fourier amplitudes of u_y and sigma_xy, H norm)
@@ -23,9 +25,10 @@
 // vectorised when V = 2).  The last tile of a row is shifted left to end at
 // nx (its overlap with the previous tile is recomputed but neither stored nor
 // counted), so every warp of a row wider than a tile is full.  The grid is
-// persistent (a multiple of the SM count) and walks tiles row-major, so the
-// halo rows a tile re-reads were fetched moments earlier by its neighbours and
-// sit in L2.  Populations carry a rim of periodic images (ghost columns and
+// persistent (a multiple of the SM count) and walks tiles row-major (the
+// TMA-staged kernel: column-major in bands of tile rows for the exact-shift
+// sets), so the halo rows a tile re-reads were fetched moments earlier by its
+// neighbours and sit in L2.  Populations carry a rim of periodic images (ghost columns and
 // rows), rewritten by every store, so no read ever wraps.
 //
 // Two step kernels share the collision code and give bitwise-identical results:
