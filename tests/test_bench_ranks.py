@@ -62,3 +62,25 @@ def test_reference_arm_line_on_rank_zero():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_record_follows_the_kernel_code_not_its_comments(tmp_path):
+    """The DRAM traffic record is reported only while the kernel sources' code matches the
+    capture; comments and blank space do not count, any code change does."""
+    csrc = tmp_path / "paper_0908_4520_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(bench.ROOT, "paper_0908_4520_gb300", "csrc")
+    for f in ("lb_kernels.cuh", "lb_device.h", "velocity_sets.h"):
+        with open(os.path.join(src, f)) as fh:
+            (csrc / f).write_text(fh.read())
+    old_root = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        d0 = bench.kernel_digest()
+        k = csrc / "lb_kernels.cuh"
+        k.write_text("// a comment\n/* and a block\n   comment */\n" + k.read_text() + "\n\n")
+        assert bench.kernel_digest() == d0
+        k.write_text(k.read_text() + "\nconstexpr int lb_extra_code = 1;\n")
+        assert bench.kernel_digest() != d0
+    finally:
+        bench.ROOT = old_root
