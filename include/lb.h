@@ -120,9 +120,11 @@ typedef struct {
     int isothermal;            /* 1: T = 1 in the equilibrium (default 0: kinetic T) */
     int diag_capacity;         /* records kept in the device ring (default 65536) */
     double storage_scale;      /* 16-bit scale S (rounded to a power of two); 0 = 2 x the initial amplitude */
-    int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel
-                                  (LB_ERR_UNSUPPORTED if not built for the storage).  Both give
-                                  bitwise-identical results. */
+    int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel;
+                                  3: TMA-staged with TMA tensor stores of each tile (FP32
+                                  Lax-Wendroff sets up to 36 velocities)
+                                  (LB_ERR_UNSUPPORTED if not built for the set or storage).  All
+                                  give bitwise-identical populations. */
     void *stream;              /* cudaStream_t to run on; NULL = a stream the handle creates */
     /* optional device allocator (e.g. PyTorch's caching allocator); both or neither */
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
@@ -163,7 +165,7 @@ typedef struct {
     double dx, dt, tau, omega;
     double c_lattice;   /* xi = c e for on-lattice sets, else 0 */
     long long time_level;   /* n: the state is f~(n dt) */
-    int tma_staged;         /* 1: steps run the TMA-staged kernel */
+    int tma_staged;         /* 1: steps run the TMA-staged kernel, 2: its store-staged variant */
     long long records;      /* diagnostics records produced so far (n + 1 after init) */
     size_t bytes_per_cell_update; /* algorithmic HBM bytes: 2 q sizeof(storage) */
     size_t device_bytes;    /* device memory held by the handle */

@@ -107,6 +107,11 @@ struct lb_handle {
     bool use_tma = false;
     int tma_ntiles_x = 0, tma_ntiles = 0, tma_x0_last = 0, tma_grid = 0;
     CUtensorMap tmap[2];
+    // store-staged TMA step kernel: its tiles, load maps (its box) and store maps (the cells of
+    // each buffer as a destination)
+    bool use_st = false;
+    int st_ntiles_x = 0, st_ntiles = 0, st_grid = 0;
+    CUtensorMap tmap_stl[2], tmap_out[2];
     long long plane = 0, origin = 0, ncell = 0;
     size_t pop_bytes = 0, device_bytes = 0;
     double dx = 0, dt = 0, tau = 0, omega = 0, scale = 1.0;
@@ -195,8 +200,9 @@ struct lb_handle {
         stream = nullptr;
     }
 
+    // tiling: 0 the plain-load kernel's, 1 the TMA-staged kernel's, 2 the store-staged kernel's
     template <class R>
-    void fill_args(lbk::Args<R>& A, bool tma) const {
+    void fill_args(lbk::Args<R>& A, int tiling) const {
         std::memset(&A, 0, sizeof(A));
         A.plane = plane;
         A.origin = origin;
@@ -204,9 +210,9 @@ struct lb_handle {
         A.ny = p.ny;
         A.pitch = pitch;
         A.gy = gy;
-        A.ntiles_x = tma ? tma_ntiles_x : ntiles_x;
-        A.ntiles = tma ? tma_ntiles : ntiles;
-        A.x0_last = tma ? tma_x0_last : x0_last;
+        A.ntiles_x = tiling == 2 ? st_ntiles_x : tiling == 1 ? tma_ntiles_x : ntiles_x;
+        A.ntiles = tiling == 2 ? st_ntiles : tiling == 1 ? tma_ntiles : ntiles;
+        A.x0_last = tiling == 2 ? 0 : tiling == 1 ? tma_x0_last : x0_last;
         A.isothermal = p.isothermal;
         A.diag_every = 1;
         const double om = std::is_same<R, float>::value ? lbh::snap_unit(omega) : omega;
@@ -242,8 +248,13 @@ lb_status launch_with(lb_handle* h, int kind, const void* src, void* dst, int ra
                       const double* i_T) {
     lbk::Args<R> A;
     const bool tma = (kind == lbk::kStepTma || kind == lbk::kMomentsTma);
-    h->fill_args(A, tma);
+    const bool st = kind == lbk::kStepTmaStore;
+    h->fill_args(A, st ? 2 : tma ? 1 : 0);
     if (tma) A.tmap = h->tmap[src == h->buf[0] ? 0 : 1];
+    if (st) {
+        A.tmap = h->tmap_stl[src == h->buf[0] ? 0 : 1];
+        A.tmap_st = h->tmap_out[dst == h->buf[0] ? 0 : 1];
+    }
     A.src = src;
     A.dst = dst;
     A.raw = raw;
@@ -289,6 +300,7 @@ lb_status launch_any(lb_handle* h, int kind, const void* src, void* dst, int raw
 lb_status step_once(lb_handle* h, int from) {
     if (h->p.force_amp != 0.0)  // the forced step runs the plain-load kernel
         return launch_any(h, lbk::kStepForced, h->buf[from], h->buf[1 - from], 0, h->grid);
+    if (h->use_st) return launch_any(h, lbk::kStepTmaStore, h->buf[from], h->buf[1 - from], 0, h->st_grid);
     if (h->use_tma) return launch_any(h, lbk::kStepTma, h->buf[from], h->buf[1 - from], 0, h->tma_grid);
     return launch_any(h, lbk::kStep, h->buf[from], h->buf[1 - from], 0, h->grid);
 }
@@ -313,6 +325,28 @@ lb_status encode_maps(lb_handle* h) {
                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return h->fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    }
+    if (h->use_st) {
+        // loads: the whole padded buffer, the store-staged kernel's box; stores: the nx x ny
+        // cells of each buffer (the rim is written by the kernel's own image stores), one
+        // tile of all q velocities per store
+        const cuuint32_t lbox[3] = {(cuuint32_t)h->shape.st_box_w, (cuuint32_t)h->shape.st_box_h,
+                                    (cuuint32_t)h->shape.box_d};
+        const cuuint64_t odims[3] = {(cuuint64_t)h->p.nx, (cuuint64_t)h->p.ny, (cuuint64_t)h->vs.q};
+        const cuuint32_t obox[3] = {(cuuint32_t)h->shape.st_tw, (cuuint32_t)h->shape.st_rows, (cuuint32_t)h->vs.q};
+        for (int i = 0; i < 2; ++i) {
+            CUresult r = enc(&h->tmap_stl[i], dt, 3, h->buf[i], dims, strides, lbox, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r == CUDA_SUCCESS) {
+                void* cells = static_cast<char*>(h->buf[i]) + h->origin * (long long)b;
+                r = enc(&h->tmap_out[i], dt, 3, cells, odims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
+            if (r != CUDA_SUCCESS)
+                return h->fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled (store-staged) failed: " + std::to_string((int)r));
+        }
     }
     return LB_OK;
 }
@@ -494,7 +528,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     if ((P.alloc == nullptr) != (P.free == nullptr)) return reject(LB_ERR_ARG, "alloc and free go together");
     if (P.kn_convention != LB_KN_LAMBDA && P.kn_convention != LB_KN_PAPER)
         return reject(LB_ERR_ARG, "unknown kn_convention");
-    if (P.step_kernel < 0 || P.step_kernel > 2) return reject(LB_ERR_ARG, "step_kernel must be 0, 1 or 2");
+    if (P.step_kernel < 0 || P.step_kernel > 3) return reject(LB_ERR_ARG, "step_kernel must be 0, 1, 2 or 3");
     if (!std::isfinite(P.force_amp) || !std::isfinite(P.force_freq))
         return reject(LB_ERR_ARG, "force_amp and force_freq must be finite");
 
@@ -585,7 +619,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         return reject(LB_ERR_CUDA, "no CUDA device");
     }
     const int occ = std::max(1, h->shape.occupancy);
-    if (P.force_amp != 0.0 && P.step_kernel == 2) {
+    if (P.force_amp != 0.0 && P.step_kernel >= 2) {
         delete h;
         return reject(LB_ERR_UNSUPPORTED, "the TMA-staged step kernel runs the free wave; forced runs use the plain kernel");
     }
@@ -597,8 +631,19 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         h->tma_grid = std::max(1, std::min(h->tma_ntiles, nsm * std::max(1, h->shape.tma_occupancy)));
         // auto: TMA staging once the grid fills a tile row and every SM gets work
         const bool big = P.nx >= ttw && h->tma_ntiles >= nsm;
-        h->use_tma = P.step_kernel == 2 || (P.step_kernel == 0 && big);
-    } else if (P.step_kernel == 2) {
+        h->use_tma = P.step_kernel >= 2 || (P.step_kernel == 0 && big);
+        // the store-staged kernel (FP32 Lax-Wendroff sets): automatic on the same grids
+        if (h->shape.st && !upwind) {
+            h->st_ntiles_x = (P.nx + h->shape.st_tw - 1) / h->shape.st_tw;
+            h->st_ntiles = h->st_ntiles_x * ((P.ny + h->shape.st_rows - 1) / h->shape.st_rows);
+            h->st_grid = std::max(1, std::min(h->st_ntiles, nsm * std::max(1, h->shape.st_occupancy)));
+            h->use_st = P.step_kernel == 3 || (P.step_kernel == 0 && h->shape.st_auto && big && h->st_ntiles >= nsm);
+        }
+        if (P.step_kernel == 3 && !h->use_st) {
+            delete h;
+            return reject(LB_ERR_UNSUPPORTED, "no store-staged TMA step kernel for this set, storage or streaming");
+        }
+    } else if (P.step_kernel >= 2) {
         delete h;
         return reject(LB_ERR_UNSUPPORTED, "no TMA-staged step kernel for this storage");
     }
@@ -610,7 +655,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
     h->sin_d = h->dalloc(rbytes * P.nx);
     h->cos_d = h->dalloc(rbytes * P.nx);
     h->partials = static_cast<double*>(
-        h->dalloc(sizeof(double) * lbk::kDiagSlots * (size_t)std::max(h->grid, h->tma_grid)));
+        h->dalloc(sizeof(double) * lbk::kDiagSlots * (size_t)std::max({h->grid, h->tma_grid, h->st_grid})));
     h->ticket = static_cast<unsigned int*>(h->dalloc(256));
     h->level_d = static_cast<long long*>(h->dalloc(256));
     h->status = static_cast<int*>(h->dalloc(256));
@@ -879,7 +924,7 @@ lb_status lb_get_info(const lb_handle* h, lb_info_t* o) {
     o->omega = h->omega;
     o->c_lattice = h->vs.c;
     o->time_level = h->level;
-    o->tma_staged = h->use_tma ? 1 : 0;
+    o->tma_staged = h->use_st ? 2 : h->use_tma ? 1 : 0;
     o->records = h->initialized ? h->level + 1 : 0;
     o->bytes_per_cell_update = 2 * (size_t)h->vs.q * storage_bytes(h->p.precision);
     o->device_bytes = h->device_bytes;

@@ -39,7 +39,8 @@ struct Tab {
 };
 
 enum Kind : int {
-    kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kStepForced = 4, kMomentsTma = 5, kQueryShape = -1
+    kStep = 0, kMoments = 1, kInit = 2, kStepTma = 3, kStepForced = 4, kMomentsTma = 5, kStepTmaStore = 6,
+    kQueryShape = -1
 };
 
 // Population layout: plane a, row y, column x at
@@ -50,6 +51,7 @@ enum Kind : int {
 template <class R>
 struct Args {
     CUtensorMap tmap;         // TMA view of src (step kernel with TMA staging only)
+    CUtensorMap tmap_st;      // TMA view of the cells of dst, nx x ny x q (store-staged kernel only)
     const void* src;          // populations read (storage type), q planes
     void* dst;                // populations written
     long long plane;          // elements per population plane ((ny + 2 gy) * pitch)
@@ -96,6 +98,10 @@ struct Shape {
     int tma_V, tma_rows, tma_threads, tma_smem, tma_occupancy;
     int tma_tw;     // cells a tile row produces (32 V, or 30 with halo lanes)
     int box_w, box_h, box_d;  // tensor-map box (x, y, velocities)
+    // store-staged TMA kernel (0 = not built for this unit): tile of st_rows x st_tw cells,
+    // load box st_box_w x st_box_h x box_d, one store box st_tw x st_rows x q per tile
+    int st, st_tw, st_rows, st_threads, st_smem, st_occupancy, st_box_w, st_box_h;
+    int st_auto;    // 1: the automatic choice prefers the store-staged kernel on large grids
 };
 
 struct Launch {

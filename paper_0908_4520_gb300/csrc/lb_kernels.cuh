@@ -421,6 +421,12 @@ struct Pack<float, 2> {
 #ifndef LB_TMA_BAND_SHIFT
 #define LB_TMA_BAND_SHIFT 4  // band height of the exact-shift sets under LB_TMA_BAND = -1
 #endif
+#ifndef LB_TMA_WIDE_WARPS
+#define LB_TMA_WIDE_WARPS 18  // consumer warps of the store-staged kernel (two per tile row)
+#endif
+#ifndef LB_TMA_WIDE_SMEM
+#define LB_TMA_WIDE_SMEM (224 * 1024)  // ring + output tile of the store-staged kernel
+#endif
 #ifndef LB_DIAG_PREFETCH
 // load sin/cos of the diagnostics before the collision: -1 per set (measured at 4096^2 FP32,
 // TMA kernel, same box: D2Q16-GH 35.7 -> 38.5 GLUPS, D2Q37 12.6 -> 12.6, D2Q36-GH
@@ -446,29 +452,42 @@ struct Cfg {
 // UPW: second-order upwind streaming of a Lax-Wendroff set (one cell per lane): lanes
 // 0, 1 and 30, 31 compute the y pass of the two columns on either side of the 28 cells
 // that lanes 2..29 own, and the box carries two extra rows above and below.
-template <class VS, class S, bool UPW = false>
+// WIDE: the store-staged variant of the Lax-Wendroff kernel (FP32, one cell per lane, halo
+// lanes): two warps share a tile row (30 cells each, 60 per row, 240 bytes: a multiple of
+// the 16-byte TMA granule), the consumer warps write the relaxed populations of the tile
+// into a shared-memory output tile, and the producer warp writes it to HBM with one TMA
+// tensor store per tile (cp.async.bulk.tensor, shared -> global), so no thread issues
+// per-velocity global stores.
+template <class VS, class S, bool UPW = false, bool WIDE = false>
 struct TmaCfg {
     static constexpr bool LW = !VS::kOnLattice;
     static constexpr int V = cells_per_lane<VS, S, LB_TMA_V>();
     static_assert(!UPW || (LW && V == 1), "upwind TMA staging: Lax-Wendroff sets, one cell per lane");
+    static_assert(!WIDE || (LW && V == 1 && !UPW && sizeof(S) == 4), "store staging: FP32 Lax-Wendroff sets");
     // consumer warps (+ one producer warp); the register cap follows from the count
     // (exact shift at 4096^2 FP32, 11 / 13 rows, GLUPS: D2Q37 18.3 / 16.8, D2Q25 21.3 / 22.3,
     // D2Q21 25.4 / 27.7, D2Q17 41.6 / 42.1, D2Q16 44.7 / 45.1, D2Q9 68.6 / 72.6)
-    static constexpr int ROWS = LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : (VS::Q > 30 ? 11 : 13));
+    static constexpr int CW = WIDE ? LB_TMA_WIDE_WARPS
+                                   : (LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : (VS::Q > 30 ? 11 : 13)));
+    static constexpr int WPR = WIDE ? 2 : 1;            // consumer warps per tile row
+    static constexpr int ROWS = CW / WPR;               // lattice rows of a tile
+    static_assert(CW % WPR == 0, "whole tile rows");
     static constexpr int TW = 32 * V;
     // Edge lanes as halo lanes (30 cells a row) and a per-tile barrier of the consumer warps,
     // chosen per set and storage by the sweep at 4096^2 / 2048^2 (GLUPS, no halo / halo /
     // halo + barrier): D2Q16 FP32 29.5 / 35.5 / 30.4; D2Q36 FP32 12.5 / 9.6 / 14.5; D2Q36
     // 16-bit 12.1 / 15.9 / 14.4; D2Q64 FP32 5.38 / 4.95 / 4.97; D2Q64 16-bit 4.37 / 6.40 / 6.28.
     static constexpr bool FP32_Q64 = sizeof(S) == 4 && VS::Q > 40;
-    static constexpr bool HALO = !UPW && LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64));
+    static constexpr bool HALO = WIDE || (!UPW && LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64)));
     static constexpr bool TILE_SYNC =
         LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && (HALO || UPW) && sizeof(S) == 4 && VS::Q == 36);
-    static constexpr int TWO = UPW ? 28 : (HALO ? 30 : TW);  // cells a tile row produces
+    static constexpr int WCELLS = UPW ? 28 : (HALO ? 30 : TW);  // cells a warp produces
+    static constexpr int TWO = WPR * WCELLS;            // cells a tile row produces
     static constexpr int GX = UPW ? 2 : 1;              // stencil reach (columns and rows) of the box
     static constexpr int BAND = LB_TMA_BAND >= 0 ? LB_TMA_BAND : (LW ? 0 : LB_TMA_BAND_SHIFT);  // tile order
     static constexpr int AL = 16 / (int)sizeof(S);      // TMA x coordinates are multiples of 16 bytes
-    static constexpr int BW = (HALO || UPW) ? 32 + AL : (LW ? TW + 2 * AL : TW + AL);
+    static_assert(!WIDE || TWO % AL == 0, "store-staged tile rows are whole 16-byte granules");
+    static constexpr int BW = WIDE ? TWO + 2 * AL : ((HALO || UPW) ? 32 + AL : (LW ? TW + 2 * AL : TW + AL));
     static constexpr int BH = LW ? ROWS + 2 * GX : ROWS;
     static constexpr int BOX = BW * BH;                 // elements of one velocity's box
     // stride of the velocity slots in a stage: dense for one 3-D box (Lax-Wendroff),
@@ -477,15 +496,18 @@ struct TmaCfg {
     static constexpr int K = LB_TMA_K > 0 ? LB_TMA_K : (LW ? (VS::Q > 40 ? 12 : 6) : 18);  // velocities per stage
     static constexpr int NG = (VS::Q + K - 1) / K;      // stages per tile
     static constexpr int STAGE_BYTES = (K * SLOT * (int)sizeof(S) + 127) / 128 * 128;
-    static constexpr int NS_FIT = LB_TMA_SMEM / STAGE_BYTES;
+    // output tile of the store-staged kernel: [velocity][row][TWO cells]
+    static constexpr int OUT_BYTES = WIDE ? (VS::Q * ROWS * TWO * (int)sizeof(S) + 127) / 128 * 128 : 0;
+    static constexpr int NS_FIT = ((WIDE ? LB_TMA_WIDE_SMEM - OUT_BYTES : LB_TMA_SMEM) - 512) / STAGE_BYTES;
     static constexpr int NS = NS_FIT < LB_TMA_NS_TILES * NG ? NS_FIT : LB_TMA_NS_TILES * NG;
-    static constexpr int THREADS = 32 * (ROWS + 1);     // + one producer warp
+    static constexpr int THREADS = 32 * (CW + 1);       // + one producer warp
     // registers a thread may hold: each SM sub-partition's 16384 registers are shared by
     // ceil(warps / 4) warps of the block (255 for 8 warps, 168 for 9..12, 128 for 13..16)
-    static constexpr int WARPS_PER_SMSP = (ROWS + 1 + 3) / 4;
+    static constexpr int WARPS_PER_SMSP = (CW + 1 + 3) / 4;
     static constexpr int MAXREG_FIT = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
     static constexpr int MAXREG = MAXREG_FIT > 255 ? 255 : MAXREG_FIT;
-    static constexpr int SMEM = NS * STAGE_BYTES + 2 * NS * 8 + 128;  // + alignment slack
+    // ring, output tile, full/empty barriers of the ring, tile-done and output-free barriers
+    static constexpr int SMEM = NS * STAGE_BYTES + OUT_BYTES + 2 * NS * 8 + 16 + 128;  // + alignment slack
     static constexpr int BOX_D = LW ? K : 1;            // velocities per TMA box
 };
 
@@ -636,6 +658,17 @@ __device__ __noinline__ void rim_images(const Args<R>& A, S* dst, int q, int x, 
         v[0] = p[0];
         if constexpr (V == 2) v[V - 1] = p[1];
         store_images<S, R, V>(A, pl, x, y, v);
+    }
+}
+
+// The same for the store-staged kernel: the values are taken from the output tile in shared
+// memory (out[a * ostride]), which the TMA store writes to (x, y) itself.
+template <class S, class R>
+__device__ __noinline__ void rim_images_tile(const Args<R>& A, S* dst, const S* out, int ostride, int q, int x, int y) {
+    for (int a = 0; a < q; ++a) {
+        S* pl = dst + (long long)a * A.plane + A.origin;
+        const S v[1] = {out[a * ostride]};
+        store_images<S, R, 1>(A, pl, x, y, v);
     }
 }
 
@@ -984,11 +1017,15 @@ __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t
 // Collision and store (or the moment outputs) of the V cells (g.x .., y) whose
 // streamed populations are in ft.  Diagnostics are reduced over the warp in
 // FP32 and added to acc (lane 0) in FP64.
-template <class VS, int N, class S, class R, int V, int KIND, class T>
+// OSTRIDE > 0 (store-staged kernel, FP32): the relaxed populations go to the output tile in
+// shared memory, out[a * OSTRIDE] for velocity a, instead of to HBM (the periodic images in
+// the ghost rim are still written here, from that tile).
+template <class VS, int N, class S, class R, int V, int KIND, class T, int OSTRIDE = 0>
 __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], S* __restrict__ dst, int y,
                                               const Lane& g, bool diag, R (&acc)[6], int lane, long long lvl,
-                                              R gt) {
+                                              R gt, S* out = nullptr) {
     constexpr int Q = VS::Q;
+    static_assert(OSTRIDE == 0 || (V == 1 && sizeof(S) == 4), "output tile: FP32, one cell per lane");
     // body force g_y(x_i, t_n) = gt sin(x_i), gt = A_f cos(phi t_n) (driven standing wave, Sec. 4);
     // compiled out of the unforced step kernels
     constexpr bool STEP = (KIND == kStep || KIND == kStepForced);
@@ -1060,7 +1097,17 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             });
         }
     }
-    if constexpr (STEP) {
+    if constexpr (STEP && OSTRIDE > 0) {
+        if (g.own) {
+            static_for<0, Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                out[a * OSTRIDE] = lane_get<0>(ft[a]);
+            });
+            if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy)
+                rim_images_tile<S, R>(A, dst, out, OSTRIDE, Q, g.x, y);
+        }
+    }
+    if constexpr (STEP && OSTRIDE == 0) {
         if (g.own) {
             S* base = dst + A.origin + (long long)y * A.pitch + g.x;
             uint32_t r0 = 0, r1 = 0;
@@ -1096,6 +1143,8 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy)
                 rim_images<S, R, V>(A, dst, Q, g.x, y);
         }
+    }
+    if constexpr (STEP) {
         // per-thread partial sums over the thread's cells of every tile; reduced once per
         // launch (warp, then FP64 across warps and blocks) in finish_step
         if (diag && g.own) {
@@ -1423,34 +1472,68 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
     }
 }
 
+// Store-staged kernel, producer side: wait (bounded) until every consumer warp has written
+// tile `ti` into the output tile, write it to the cells (x0.., y0..) of dst with one TMA
+// tensor store (velocities, rows and columns of the tile; the tensor map clips it at nx and
+// ny), wait until the store has read the output tile, and release it.  False on a timeout.
+__device__ __forceinline__ bool store_tile(const Args<float>& A, const void* otile, uint64_t* tdone, uint64_t* ofree,
+                                           int ti, int x0, int y0) {
+    if (!mbar_wait(tdone, (uint32_t)ti & 1u, A.status)) return false;
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(&A.tmap_st)),
+        "r"(smem_u32(otile)), "r"(x0), "r"(y0), "r"(0)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    mbar_arrive(ofree);
+    return true;
+}
+
 // KIND = kStep: one level (store f*, diagnostics, level advance); kMoments: the per-cell
 // moments (and optionally f~) of the current level, nothing stored, no level advance.
-template <class VS, int N, class S, bool UPW = false, int KIND = kStep>
-__global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
+// WIDE (KIND = kStep only): the store-staged variant (see TmaCfg): consumer warp w owns half
+// w % 2 of tile row w / 2; at the end of a tile each consumer warp writes its relaxed cells
+// into the output tile, then arrives on the tile-done barrier; the producer, once it has
+// issued the next tile's loads, waits for that barrier, writes the tile to HBM with one TMA
+// tensor store, waits until the store has read the output tile and releases it (the
+// output-free barrier) for the consumers' next tile.
+template <class VS, int N, class S, bool UPW = false, int KIND = kStep, bool WIDE = false>
+__global__ void __maxnreg__((TmaCfg<VS, S, UPW, WIDE>::MAXREG))
     lb_tma_step_kernel(const __grid_constant__ Args<float> A) {
     static_assert(KIND == kStep || KIND == kMoments, "TMA-staged kinds: step, moments");
+    static_assert(!WIDE || KIND == kStep, "the store-staged kernel is a step kernel");
     using R = float;
-    using C = TmaCfg<VS, S, UPW>;
-    constexpr int Q = VS::Q, V = C::V, ROWS = C::ROWS, TW = C::TW, AL = C::AL;
+    using C = TmaCfg<VS, S, UPW, WIDE>;
+    constexpr int Q = VS::Q, V = C::V, ROWS = C::ROWS, CW = C::CW, TW = C::TW, AL = C::AL;
     constexpr int NS = C::NS, NG = C::NG, K = C::K, BW = C::BW, BOX = C::BOX, SLOT = C::SLOT;
     constexpr int STAGE_ELEMS = C::STAGE_BYTES / (int)sizeof(S);
+    constexpr int OSTRIDE = WIDE ? ROWS * C::TWO : 0;  // output tile: elements per velocity
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations must be 128-byte aligned: align the base explicitly
     unsigned char* const smem_raw =
         smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     S* const stages = reinterpret_cast<S*>(smem_raw);
-    uint64_t* const full = reinterpret_cast<uint64_t*>(smem_raw + NS * C::STAGE_BYTES);
+    S* const otile = reinterpret_cast<S*>(smem_raw + NS * C::STAGE_BYTES);
+    uint64_t* const full = reinterpret_cast<uint64_t*>(smem_raw + NS * C::STAGE_BYTES + C::OUT_BYTES);
     uint64_t* const empty = full + NS;
+    uint64_t* const tdone = empty + NS;  // store-staged: the consumers have filled the output tile
+    uint64_t* const ofree = tdone + 1;   // store-staged: the output tile may be overwritten
     __shared__ int s_abort;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], ROWS);
+            mbar_init(&empty[s], CW);
+        }
+        if constexpr (WIDE) {
+            mbar_init(tdone, CW);
+            mbar_init(ofree, 1);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if constexpr (WIDE) mbar_arrive(ofree);  // phase 0: the output tile starts free
     }
     __syncthreads();
 
@@ -1459,14 +1542,16 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
     R acc[6] = {0, 0, 0, 0, 0, 0};
     volatile int* abort_flag = &s_abort;
 
-    if (warp == ROWS) {
+    if (warp == CW) {
         // ---------------- producer: one thread streams the boxes of every tile
         if (lane == 0) {
             uint32_t it = 0;
+            int ti = 0, px0 = 0, py0 = 0;  // store-staged: tiles issued, coordinates of the last
             for (int tile = blockIdx.x; tile < A.ntiles && !*abort_flag; tile += gridDim.x) {
                 int ty, tx;
                 tma_tile_coords<C::BAND>(tile, A.ntiles_x, A.ntiles, ty, tx);
-                const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tx * C::TWO;
+                // store-staged tiles are not shifted: the store clips the last one at nx
+                const int x0 = (!WIDE && tx == A.ntiles_x - 1) ? A.x0_last : tx * C::TWO;
                 const int y0 = ty * ROWS;
                 for (int grp = 0; grp < NG; ++grp, ++it) {
                     const int s = (int)(it % NS);
@@ -1482,7 +1567,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                     S* dstage = stages + (long long)s * STAGE_ELEMS;
                     if constexpr (C::LW) {
                         mbar_arrive_expect_tx(&full[s], (uint32_t)(K * BOX * sizeof(S)));
-                        const int xs = ((x0 - C::GX + kGhostX) / AL) * AL;
+                        const int xs = WIDE ? x0 - AL + kGhostX : ((x0 - C::GX + kGhostX) / AL) * AL;
                         tma_load_3d(dstage, &A.tmap, &full[s], xs, y0 - C::GX + A.gy, a0);
                     } else {
                         mbar_arrive_expect_tx(&full[s], (uint32_t)(na * BOX * sizeof(S)));
@@ -1493,6 +1578,18 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                         }
                     }
                 }
+                if constexpr (WIDE) {
+                    // the previous tile's output, once this tile's loads are on their way
+                    if (ti > 0 && !*abort_flag && !store_tile(A, otile, tdone, ofree, ti - 1, px0, py0)) *abort_flag = 1;
+                    px0 = x0;
+                    py0 = y0;
+                    ++ti;
+                }
+            }
+            if constexpr (WIDE) {
+                if (ti > 0 && !*abort_flag && !store_tile(A, otile, tdone, ofree, ti - 1, px0, py0)) *abort_flag = 1;
+                // every store has written HBM before the block exits
+                asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
             }
             // drain: no box may still be in flight when the block exits
             if (*abort_flag) {
@@ -1505,12 +1602,16 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
         // stage index and parity advance with the stream of groups (NG per tile)
         int st_i = 0;
         uint32_t st_ph = 0;
-        for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        // store-staged: the warp's row of the tile and its half of the row
+        const int trow = WIDE ? warp / C::WPR : warp;
+        const int half = WIDE ? warp % C::WPR : 0;
+        uint32_t ti = 0;  // tiles processed (store-staged: phase of the output-free barrier)
+        for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++ti) {
             int ty, tx;
             tma_tile_coords<C::BAND>(tile, A.ntiles_x, A.ntiles, ty, tx);
-            const int tile_start = tx * C::TWO;
-            const int x0 = (tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
-            const int y = ty * ROWS + warp;
+            const int tile_start = tx * C::TWO + half * C::WCELLS;
+            const int x0 = (!WIDE && tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
+            const int y = ty * ROWS + trow;
             const Lane g = UPW      ? upwind_lane_geometry(lane, x0, tile_start, A.nx)
                            : C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx)
                                      : lane_geometry<V>(lane, x0, tile_start, A.nx);
@@ -1519,7 +1620,8 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
             bool ok = !*abort_flag;
             // Lax-Wendroff: column of this lane's first cell in the box row, and the column
             // whose y-pass the two warp-edge lanes need (x0 - 1 for lane 0, x0 + TW for lane 31)
-            const int r_lw = (x0 - 1 + kGhostX) & (AL - 1);
+            // (store-staged: the box starts AL columns left of the tile row)
+            const int r_lw = WIDE ? AL - 1 + half * C::WCELLS : (x0 - 1 + kGhostX) & (AL - 1);
             const int c_lw = C::HALO ? r_lw + lane : r_lw + 1 + lane * V;
             const int ce_lw = (lane == 31) ? r_lw + 1 + TW : r_lw;
             static_for<0, NG>([&](auto gc) {
@@ -1547,7 +1649,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                                 const R yf = A.tab.uw[iy][0], yn = A.tab.uw[iy][1], ys = A.tab.uw[iy][2];
                                 const R xf = A.tab.uw[ix][0], xn = A.tab.uw[ix][1], xs = A.tab.uw[ix][2];
                                 const int c = ((x0 - 2 + kGhostX) & (AL - 1)) + lane;
-                                const S* r0 = box + (warp + 2) * BW;
+                                const S* r0 = box + (trow + 2) * BW;
                                 const S* rn = r0 - sy * BW;
                                 const S* rf = r0 - 2 * sy * BW;
                                 const R gv = fma(yf, sld1<S, R>(rf + c, one),
@@ -1567,7 +1669,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                                 constexpr int ix = VS::ix(a), iy = VS::iy(a);
                                 const R ly0 = A.tab.lw[iy][0], ly1 = A.tab.lw[iy][1], ly2 = A.tab.lw[iy][2];
                                 const R lx0 = A.tab.lw[ix][0], lx1 = A.tab.lw[ix][1], lx2 = A.tab.lw[ix][2];
-                                const S* rm = box + warp * BW;
+                                const S* rm = box + trow * BW;
                                 const S* r0 = rm + BW;
                                 const S* rp = r0 + BW;
                                 if constexpr (C::HALO) {
@@ -1618,7 +1720,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                             } else {
                                 constexpr int ex = VS::ex(a);
                                 const int r = (x0 - ex + kGhostX) & (AL - 1);
-                                const S* p = box + warp * BW + r + lane * V;
+                                const S* p = box + trow * BW + r + lane * V;
                                 if constexpr (V == 2 && (ex % 2 == 0)) {
                                     R v0, v1;
                                     sld2<S, R>(p, sc, v0, v1);
@@ -1639,20 +1741,39 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW>::MAXREG))
                     st_ph ^= 1u;
                 }
             });
-            if (ok && y < A.ny)
-                collide_store<VS, N, S, R, V, KIND>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0));
+            if constexpr (WIDE) {
+                // the output tile is free once the producer's store of the previous tile has read it
+                if (ok) {
+                    ok = mbar_wait(ofree, ti & 1u, A.status);
+                    if (!ok) *abort_flag = 1;
+                }
+                if (ok && y < A.ny)
+                    collide_store<VS, N, S, R, V, KIND, typename Pack<R, V>::T, OSTRIDE>(
+                        A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl, R(0),
+                        otile + trow * C::TWO + (g.x - tx * C::TWO));
+                // the generic-proxy writes of the tile become visible to the TMA store; a warp
+                // whose wait ran out does not arrive, so the producer's bounded wait runs out
+                // too and no store of the tile is issued
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (ok && lane == 0) mbar_arrive(tdone);
+            } else {
+                if (ok && y < A.ny)
+                    collide_store<VS, N, S, R, V, KIND>(A, ft, static_cast<S*>(A.dst), y, g, diag, acc, lane, lvl,
+                                                        R(0));
+            }
             if constexpr (C::TILE_SYNC) {
                 // keep the consumer warps within one tile of each other, so a stage is
                 // released (and refilled) as soon as the last of them has read it; every
                 // consumer warp reaches this barrier once per tile (its waits are bounded)
-                asm volatile("bar.sync 1, %0;" ::"r"(ROWS * 32) : "memory");
+                asm volatile("bar.sync 1, %0;" ::"r"(CW * 32) : "memory");
                 if (*abort_flag) ok = false;
             }
             if (!ok) break;
         }
     }
     __syncthreads();
-    if constexpr (KIND == kStep) finish_step<R, ROWS>(A, acc, lvl, diag, warp, lane);
+    if constexpr (KIND == kStep) finish_step<R, CW>(A, acc, lvl, diag, warp, lane);
 }
 
 // ------------------------------------------------------------ init kernel
@@ -1695,6 +1816,9 @@ cudaError_t launch_typed(const Launch& L) {
     // for FP32 storage
     constexpr bool kUpw = !VS::kOnLattice && !Is16<S>::value;
     constexpr bool kUpwTma = kUpw && kTma && std::is_same<S, float>::value;
+    // store-staged TMA kernel: FP32 Lax-Wendroff sets up to 36 velocities (the output tile of
+    // a 64-velocity set leaves too little shared memory for the ring)
+    constexpr bool kStore = kTma && !VS::kOnLattice && std::is_same<S, float>::value && VS::Q <= 40;
     if (L.kind == kQueryShape) {
         Shape* sh = static_cast<Shape*>(const_cast<void*>(L.args));
         sh->V = C::V;
@@ -1736,6 +1860,27 @@ cudaError_t launch_typed(const Launch& L) {
                 if (e == cudaSuccess)
                     e = cudaFuncSetAttribute(lb_tma_step_kernel<VS, N, S, false, kMoments>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+            }
+            sh->st = 0;
+            if constexpr (kStore) {
+                using TS = TmaCfg<VS, S, false, true>;
+                auto kernel = lb_tma_step_kernel<VS, N, S, false, kStep, true>;
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh->st_occupancy, kernel, TS::THREADS, TS::SMEM);
+                if (e == cudaSuccess) {
+                    sh->st = sh->st_occupancy > 0 ? 1 : 0;
+                    sh->st_tw = TS::TWO;
+                    sh->st_rows = TS::ROWS;
+                    sh->st_threads = TS::THREADS;
+                    sh->st_smem = TS::SMEM;
+                    sh->st_box_w = TS::BW;
+                    sh->st_box_h = TS::BH;
+                    // measured at 4096^2 (GLUPS, TMA-staged / store-staged): D2Q36-GH N = 3 13.8 /
+                    // 16.2, N = 2 11.4 / 16.9, N = 1 9.8 / 18.1; D2Q16-GH N = 2 38.2 / 31.5
+                    sh->st_auto = VS::Q > 16 ? 1 : 0;
+                }
             }
         }
         return e;
@@ -1795,6 +1940,13 @@ cudaError_t launch_typed(const Launch& L) {
         case kMomentsTma:
             if constexpr (kTma) {
                 lb_tma_step_kernel<VS, N, S, false, kMoments><<<L.grid, T::THREADS, T::SMEM, L.stream>>>(A);
+                break;
+            }
+            return cudaErrorNotSupported;
+        case kStepTmaStore:
+            if constexpr (kStore) {
+                using TS = TmaCfg<VS, S, false, true>;
+                lb_tma_step_kernel<VS, N, S, false, kStep, true><<<L.grid, TS::THREADS, TS::SMEM, L.stream>>>(A);
                 break;
             }
             return cudaErrorNotSupported;

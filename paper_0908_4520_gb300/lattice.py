@@ -14,7 +14,8 @@ class Lattice:
     precision: "f32" (default), "f64", "bf16", "f16" (16-bit: GH sets only).
     stream: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
     or None for a stream the handle creates.
-    step_kernel: "auto", "plain" (coalesced loads) or "tma" (TMA-staged); same results.
+    step_kernel: "auto", "plain" (coalesced loads), "tma" (TMA-staged) or "tma_store" (TMA-staged
+    with TMA tensor stores; FP32 Lax-Wendroff sets up to 36 velocities); same results.
     force_amp, force_freq: body force g_y = force_amp sin(x_i) cos(force_freq t) driving the
     standing shear wave (0: free decay).
     n_eq: Hermite order N of the equilibrium, 1..4 (1: f^eq = w rho (1 + xi.u)).
@@ -39,7 +40,7 @@ class Lattice:
         p.diag_capacity = diag_capacity
         p.storage_scale = storage_scale
         p.stream = stream
-        p.step_kernel = {"auto": 0, "plain": 1, "tma": 2}[step_kernel]
+        p.step_kernel = {"auto": 0, "plain": 1, "tma": 2, "tma_store": 3}[step_kernel]
         p.force_amp, p.force_freq = force_amp, force_freq
         p.test_withhold_stage = int(test_withhold_stage)
         p.scheme = capi.SCHEMES[scheme]

@@ -5,10 +5,11 @@ Tolerances:
   rounding; the deviations f - w agree within f64_tol(steps, u0) (the
   oracle's own rounding, which works on the full f, relative to the signal).
 * FP32: u_y within 1e-6 relative L2 (the stated bound for the FP32
-  collide-stream) on short runs; on longer runs, and for sigma_xy (whose size
-  is ~Kn k U0, so its relative error is amplified by |u|/|sigma|), the bound
-  derived from FP32 storage rounding, f32_tol(steps) relative to the velocity
-  amplitude.
+  collide-stream), at 20 levels and at the benchmark's 2000 levels (Kn = 0.1,
+  2-D on 256 x 8 and row by row at 4096 x 4096).  sigma_xy (size ~Kn k U0,
+  formed by cancellation between moments of size U0) is bounded relative to
+  the u_y norm: f32_tol(steps) on the short random-field runs, 1e-6 on the
+  2000-level runs.
 Grids span several tiles with ragged tails in both directions (tile = 8 rows
 x 64 columns, or 32 columns for D2Q64-GH).
 """
@@ -57,14 +58,22 @@ def test_f32_moments_match_oracle(quad, N):
     assert np.max(np.abs(rec["amp"] - d[:, 4])) < 1e-6 * np.max(np.abs(d[:, 4]))
 
 
-@pytest.mark.parametrize("quad,N", [("D2Q36-GH", 3), ("D2Q37", 3), ("D2Q25", 4)])
-def test_f32_longer_run_within_storage_bound(quad, N):
-    L, P, f, d, capi = run_both(quad, N, 100, 11, 0.3, "f32", 200, u0=1e-3, u1=1e-3)
+@pytest.mark.parametrize("quad", ["D2Q36-GH", "D2Q37"])
+def test_f32_2000_steps_within_1e6(quad):
+    """The benchmark's run length (2000 levels) on a 2-D 256 x 8 grid, u1 != 0, Kn = 0.1:
+    u_y within 1e-6 relative L2 of the oracle, and the amplitude A(n) within 1e-6 of its
+    scale at every level.  sigma_xy ~ Kn k U0 is formed by cancellation between moments
+    of size U0; its error is bounded relative to the u_y norm (the same units)."""
+    L, P, f, d, capi = run_both(quad, 3, 256, 8, 0.1, "f32", 2000, u0=1e-3, u1=1e-3, diag_capacity=2008)
     m = L.moments()
     o = P.moments(f)
+    assert rel_l2(m["uy"], o["uy"]) < 1e-6
     unorm = np.linalg.norm(o["uy"])
-    assert np.linalg.norm(m["uy"] - o["uy"]) / unorm < f32_tol(200)
-    assert np.linalg.norm(m["sxy"] - o["sxy"]) / unorm < f32_tol(200)
+    assert np.linalg.norm(m["sxy"] - o["sxy"]) / unorm < 1e-6
+    rec = L.diagnostics()
+    assert len(rec) == 2001
+    assert np.max(np.abs(rec["amp"] - d[:, 4])) < 1e-6 * np.max(np.abs(d[:, 4]))
+    L.close()
 
 
 @pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 2, 1), ("D2Q37", 2, 2, 1), ("D2Q25", 3, 6, 3),
@@ -182,7 +191,7 @@ def test_full_size_rows_match_oracle(quad):
     solution does not depend on y, so every row must equal the oracle's 4096 x 1 run."""
     Lattice, capi = lib()
     L = Lattice(quad, 3, 4096, 4096, 0.1).init_shear_wave(1e-3, 0.0)
-    assert L.info["tma_staged"] == 1
+    assert L.info["tma_staged"] == (2 if quad.endswith("-GH") else 1)
     L.step(12)
     m = L.moments()
     P = oracle.Problem(quad, 3, 4096, 1, 0.1)
@@ -194,6 +203,34 @@ def test_full_size_rows_match_oracle(quad):
         assert rel_l2(m["uy"][row], o["uy"][0]) < 1e-6
         assert np.linalg.norm(m["sxy"][row] - o["sxy"][0]) / unorm < f32_tol(12)
     L.close()
+
+
+@pytest.mark.parametrize("quad", ["D2Q36-GH", "D2Q37"])
+def test_full_size_2000_steps_rows_match_oracle(quad):
+    """4096 x 4096, N = 3, FP32, Kn = 0.1, the benchmark's launch configuration and run
+    length.  With u1 = 0 every row equals the oracle's 4096 x 1 run: sampled rows of u_y
+    within 1e-6 relative L2 after 2000 levels, sigma_xy within 1e-6 of the u_y norm, and
+    the decay rate (the oracle's fit rule on both histories) within 1e-5."""
+    Lattice, capi = lib()
+    L = Lattice(quad, 3, 4096, 4096, 0.1, diag_capacity=2008).init_shear_wave(1e-3, 0.0)
+    assert L.info["tma_staged"] == (2 if quad.endswith("-GH") else 1)
+    L.step(2000)
+    m = L.moments()
+    rec = L.diagnostics()
+    L.close()
+    P = oracle.Problem(quad, 3, 4096, 1, 0.1)
+    f = P.init_shear(1e-3)
+    d = P.run(f, 2000)
+    o = P.moments(f)
+    rows = slice(0, 4096, 97)
+    ub = np.broadcast_to(o["uy"][0], m["uy"][rows].shape)
+    sb = np.broadcast_to(o["sxy"][0], m["sxy"][rows].shape)
+    assert rel_l2(m["uy"][rows], ub) < 1e-6
+    assert np.linalg.norm(m["sxy"][rows] - sb) / np.linalg.norm(ub) < 1e-6
+    t0 = min(5.0 * P.tau, d[-1, 0] / 4.0)
+    r_gpu = oracle.decay_fit(rec["t"], rec["amp"], t0)
+    r_ora = oracle.decay_fit(d[:, 0], d[:, 4], t0)
+    assert abs(r_gpu / r_ora - 1.0) < 1e-5, (r_gpu, r_ora)
 
 
 @pytest.mark.parametrize("quad,N,prec,nx,ny", [("D2Q36-GH", 3, "f32", 256, 40), ("D2Q37", 3, "f32", 200, 19),
@@ -249,3 +286,22 @@ def test_diagnostics_at_reads_each_level_while_the_next_runs():
     assert e.value.status == capi.LB_ERR_ARG
     with pytest.raises(capi.LBError):
         capi.lb_diagnostics_at(L.h, 75)  # not produced yet
+
+
+@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 256, 40), ("D2Q36-GH", 3, 130, 17), ("D2Q16-GH", 2, 64, 8),
+                                          ("D2Q16-GH", 4, 34, 20), ("D2Q36-GH", 2, 61, 9)])
+def test_store_staged_and_plain_kernels_are_bitwise_equal(quad, N, nx, ny):
+    """The TMA-staged kernel with TMA tensor stores of each tile (60-column tiles, clipped at
+    nx and ny; the periodic images in the rim written by the boundary lanes) gives the
+    plain-load kernel's populations bit for bit."""
+    Lattice, capi = lib()
+    a = Lattice(quad, N, nx, ny, 0.1, step_kernel="tma_store").init_shear_wave(1e-3, 1e-3)
+    b = Lattice(quad, N, nx, ny, 0.1, step_kernel="plain").init_shear_wave(1e-3, 1e-3)
+    assert a.info["tma_staged"] == 2 and b.info["tma_staged"] == 0
+    a.step(37)
+    b.step(37)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    ra, rb = a.diagnostics(), b.diagnostics()
+    np.testing.assert_allclose(ra["amp"], rb["amp"], rtol=1e-6, atol=1e-15)
+    a.close()
+    b.close()

@@ -1,0 +1,116 @@
+"""16-bit deviation storage (BF16, FP16; FP32 arithmetic) against the FP64 oracle.
+
+The stored value of population a is h_a = d_a / s_a, d_a = f~_a - w_a rho0 its
+deviation and s_a a power of two near w_a S (S = 2 U0).  Every store rounds h_a
+stochastically to a format with m explicit mantissa bits (FP16: m = 10, BF16:
+m = 7): the error e_a has mean zero and |e_a| < ulp(h_a) <= 2^-m |h_a|, so its
+standard deviation in units of d is at most 2^-(m+1) |d_a|.  In the linear
+standing shear wave every population is a translate of its initial deviation,
+|d_a| <= w_a |xi_ya| U0, so one step adds to the u_y of a cell a noise
+sum_a xi_ya e_a s_a of standard deviation at most
+
+    sigma U0,   sigma = 2^-(m+1) sqrt(sum_a w_a^2 xi_ya^4).
+
+The collide-stream step does not amplify it (BGK relaxation with 0 < omega < 2
+and Lax-Wendroff with |C| <= 1 are contractions), so after n steps it has
+grown at most like a random walk:
+
+* u_y field: rms error <= sqrt(n) sigma U0, i.e. sqrt(2 n) sigma relative to
+  the initial rms U0 / sqrt(2);
+* amplitude A = 2/(nx ny) sum u_y sin(x_i): standard deviation
+  <= sqrt(2 n / (nx ny)) sigma U0.
+
+The tests assert three of these standard deviations plus the FP32 arithmetic
+allowance n omega 2^-24 (a relative bias of the FP32 equilibrium's conserved
+moments of at most one unit roundoff per collision, accumulated over the run).
+The decay rate, fitted by the oracle's least-squares rule on both histories
+over the same window, must agree within 1e-3 relative: the stated bound for
+reduced-precision storage.
+
+Grid: 130 x 1024 on the TMA-staged kernel (tiles of 30 columns x 15 / 19 rows:
+ragged in both directions); u_y = U0 sin(x) does not depend on y, so every row
+is compared with the oracle's 130 x 1 run.  Kn spans the seeded precision draw
+(its smallest, middle and largest values) for D2Q64-GH, N = 4, and the
+benchmark's Kn = 0.1 for D2Q36-GH, N = 3.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from lbtest import lib
+from paper_0908_4520_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U0 = 1e-4
+STEPS = 2000
+NX, NY = 130, 1024
+MANTISSA = {"f16": 10, "bf16": 7}
+
+_KN = sorted(inputs.precision_kn())
+CASES = [("D2Q64-GH", 4, _KN[0]), ("D2Q64-GH", 4, _KN[4]), ("D2Q64-GH", 4, _KN[-1]), ("D2Q36-GH", 3, 0.1)]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(quad, N, kn):
+    P = oracle.Problem(quad, N, NX, 1, kn)
+    f = P.init_shear(U0)
+    d = P.run(f, STEPS)
+    return P, d, P.moments(f)["uy"][0].copy()
+
+
+def sigma(P, prec):
+    """Per-step u_y noise of one cell, in units of U0 (see the module docstring)."""
+    w, xi_y = P.vs.w, P.vs.xi[:, 1]
+    return 2.0 ** -(MANTISSA[prec] + 1) * math.sqrt(float(np.sum(w * w * xi_y ** 4)))
+
+
+def window(P, t):
+    return min(5.0 * P.tau, t[-1] / 4.0)
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("quad,N,kn", CASES)
+def test_sixteen_bit_storage_against_oracle(quad, N, kn, prec):
+    Lattice, capi = lib()
+    L = Lattice(quad, N, NX, NY, kn, precision=prec, step_kernel="tma", diag_capacity=STEPS + 8)
+    L.init_shear_wave(U0)
+    assert L.info["tma_staged"] == 1
+    L.step(STEPS)
+    rec = L.diagnostics()
+    uy = L.moments()["uy"]
+    omega = L.info["omega"]
+    L.close()
+    P, d, uy_o = oracle_run(quad, N, kn)
+    s = sigma(P, prec)
+    f32_allow = STEPS * omega * 2.0 ** -24
+    # decay rate: the same fit on both histories
+    t0 = window(P, d[:, 0])
+    r_gpu = oracle.decay_fit(rec["t"], rec["amp"], t0)
+    r_ora = oracle.decay_fit(d[:, 0], d[:, 4], t0)
+    assert abs(r_gpu / r_ora - 1.0) < 1e-3, (r_gpu, r_ora)
+    # amplitude history
+    amp_err = np.max(np.abs(rec["amp"] - d[:, 4])) / U0
+    amp_bound = 3.0 * math.sqrt(2.0 * STEPS / (NX * NY)) * s + f32_allow
+    assert amp_err < amp_bound, (amp_err, amp_bound)
+    # u_y field, every row against the oracle's row, relative to the initial rms
+    du = uy - uy_o[None, :]
+    field_err = np.sqrt(np.mean(du * du)) / (U0 / math.sqrt(2.0))
+    field_bound = 3.0 * math.sqrt(2.0 * STEPS) * s + f32_allow
+    assert field_err < field_bound, (field_err, field_bound)
+
+
+def test_library_fit_equals_the_oracle_rule():
+    """lb_fit_decay (FP64, on the device records) and the oracle's fit give the same rate."""
+    Lattice, capi = lib()
+    L = Lattice("D2Q36-GH", 3, NX, 64, 0.1, precision="f16", diag_capacity=STEPS + 8).init_shear_wave(U0)
+    L.step(STEPS)
+    rec = L.diagnostics()
+    t0 = min(5.0 * L.info["tau"], rec["t"][-1] / 4.0)
+    r_lib = L.fit_decay(t0)[0]
+    r_np = oracle.decay_fit(rec["t"], rec["amp"], t0)
+    assert abs(r_lib / r_np - 1.0) < 1e-10
+    L.close()

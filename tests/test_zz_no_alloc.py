@@ -1,6 +1,8 @@
 """lb_solve_static (fixed device scratch, no allocation) against an lb_batch run of the same instance.
 
-Collected last on purpose: it must pass in a fresh process and after every other test.
+Collected last on purpose: a failure here stops a run only after every other test
+has run.  One test starts a fresh process whose first CUDA call is the entry
+point itself.
 """
 import numpy as np
 import pytest
@@ -83,3 +85,51 @@ def test_oversize_solve_is_rejected_before_any_work():
     # and a valid call still works afterwards
     amp, _, st = capi.lb_solve_static(_desc(capi, *CASES[1]))
     assert st.level == CASES[1][5] + 1 and np.all(np.isfinite(amp))
+
+
+def _free_device_bytes():
+    import torch
+
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_calls_allocate_no_device_memory():
+    """After one call per precision (the first call of a kernel may load its module), further
+    calls of other sizes and precisions leave the device's free memory unchanged."""
+    Lattice, capi = lib()
+    _free_device_bytes()  # the caller's own CUDA set-up comes first
+    for prec in ("f32", "f16", "bf16"):
+        capi.lb_solve_static(_desc(capi, *CASES[1]), precision=capi.PRECISIONS[prec])
+    before = _free_device_bytes()
+    for case in CASES:
+        for prec in ("f32", "f16", "bf16"):
+            amp, _, st = capi.lb_solve_static(_desc(capi, *case), precision=capi.PRECISIONS[prec])
+            assert st.status == 0 and np.all(np.isfinite(amp))
+    assert _free_device_bytes() == before
+
+
+def test_first_cuda_action_of_a_fresh_process():
+    """A process whose first CUDA call is lb_solve_static (the call that finds the array's
+    device address) returns the same history as the batch entry point."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    Lattice, capi = lib()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = (
+        "import json, sys\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_0908_4520_gb300 import capi\n"
+        f"d = capi.lb_instance_desc(capi.QUADRATURES[{CASES[0][0]!r}], {CASES[0][1]}, {CASES[0][2]}, {CASES[0][3]}, "
+        f"{CASES[0][4]}, 1e-3, {CASES[0][5]}, {CASES[0][6]})\n"
+        "amp, shear, st = capi.lb_solve_static(d)\n"
+        "print(json.dumps({'amp': list(map(float, amp)), 'level': st.level, 'status': st.status}))\n")
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    ref_amp, _, ref_st = _batch_history(CASES[0])
+    assert got["status"] == 0 and got["level"] == ref_st["level"]
+    assert _close(np.array(got["amp"]), ref_amp, 2e-6)
