@@ -122,7 +122,7 @@ typedef struct {
     double storage_scale;      /* 16-bit scale S (rounded to a power of two); 0 = 2 x the initial amplitude */
     int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel;
                                   3: TMA-staged with TMA tensor stores of each tile (FP32
-                                  Lax-Wendroff sets up to 36 velocities)
+                                  Lax-Wendroff sets up to 36 velocities, nx a multiple of 4)
                                   (LB_ERR_UNSUPPORTED if not built for the set or storage).  All
                                   give bitwise-identical populations. */
     void *stream;              /* cudaStream_t to run on; NULL = a stream the handle creates */

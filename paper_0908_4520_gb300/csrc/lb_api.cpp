@@ -234,8 +234,23 @@ struct lb_handle {
         A.ring = ring;
         A.ring_cap = p.diag_capacity;
         A.status = status;
-        lbh::build_tab<R>(vs, dt, dx, scale, A.tab);
+        // the kernel tables (and the relaxation tables of this omega), built once per storage scale
+        if (tab_scale != scale) {
+            lbh::build_tab<float>(vs, dt, dx, scale, tab_f);
+            lbh::build_relax<float>(vs, (float)lbh::snap_unit(omega), tab_f);
+            lbh::build_tab<double>(vs, dt, dx, scale, tab_d);
+            lbh::build_relax<double>(vs, omega, tab_d);
+            tab_scale = scale;
+        }
+        if constexpr (std::is_same<R, float>::value) {
+            A.tab = tab_f;
+        } else {
+            A.tab = tab_d;
+        }
     }
+    mutable lbk::Tab<float> tab_f;
+    mutable lbk::Tab<double> tab_d;
+    mutable double tab_scale = -1.0;
 
 };
 
@@ -632,8 +647,10 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         // auto: TMA staging once the grid fills a tile row and every SM gets work
         const bool big = P.nx >= ttw && h->tma_ntiles >= nsm;
         h->use_tma = P.step_kernel >= 2 || (P.step_kernel == 0 && big);
-        // the store-staged kernel (FP32 Lax-Wendroff sets): automatic on the same grids
-        if (h->shape.st && !upwind) {
+        // the store-staged kernel (FP32 Lax-Wendroff sets): automatic on the same grids.  Its
+        // stores cover whole 16-byte granules of a row, so nx must be a multiple of 4 (else the
+        // store of the last tile would reach the periodic images past nx)
+        if (h->shape.st && !upwind && P.nx % 4 == 0) {
             h->st_ntiles_x = (P.nx + h->shape.st_tw - 1) / h->shape.st_tw;
             h->st_ntiles = h->st_ntiles_x * ((P.ny + h->shape.st_rows - 1) / h->shape.st_rows);
             h->st_grid = std::max(1, std::min(h->st_ntiles, nsm * std::max(1, h->shape.st_occupancy)));
@@ -641,7 +658,8 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         }
         if (P.step_kernel == 3 && !h->use_st) {
             delete h;
-            return reject(LB_ERR_UNSUPPORTED, "no store-staged TMA step kernel for this set, storage or streaming");
+            return reject(LB_ERR_UNSUPPORTED,
+                          "no store-staged TMA step kernel for this set, storage, streaming or nx (a multiple of 4)");
         }
     } else if (P.step_kernel >= 2) {
         delete h;

@@ -333,6 +333,14 @@ lb_status lb_batch_add(lb_batch* b, const lb_instance_desc* d, int* slot) {
     const double tau = b->p.kn_convention == LB_KN_LAMBDA ? d->kn * std::sqrt(2.0 / M_PI) : d->kn;
     const double omega = lbh::snap_unit(dt / (tau + 0.5 * dt));
     in.omega = (float)omega;
+    {
+        lbk::Tab<float> rt = b->args.tab[si];
+        lbh::build_relax<float>(b->sets[si], in.omega, rt);
+        std::memcpy(in.ow, rt.ow, sizeof(in.ow));
+        std::memcpy(in.owlo, rt.owlo, sizeof(in.owlo));
+        std::memcpy(in.hn1lo, rt.hn1lo, sizeof(in.hn1lo));
+        std::memcpy(in.whn1lo, rt.whn1lo, sizeof(in.whn1lo));
+    }
     in.sigma_fac = (float)(1.0 - 0.5 * omega);
     in.scale = (float)lbh::pow2_near(std::max(2.0 * std::fabs(d->u0), 1e-6));
     in.stop_ratio2 = (float)(d->stop_ratio * d->stop_ratio);

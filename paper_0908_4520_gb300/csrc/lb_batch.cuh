@@ -40,6 +40,15 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
     const int ncell = nx * ny;
     const long long pop = (long long)Q * ncell;
     const float omega = in.omega, sigma_fac = in.sigma_fac;
+    // the instance's relaxation tables (omega W_i and the second terms), in registers
+    float ow_i[VS::NA], owlo_i[VS::NA], hn1lo_i[VS::NA], whn1lo_i[VS::NA];
+#pragma unroll
+    for (int i = 0; i < VS::NA; ++i) {
+        ow_i[i] = in.ow[i];
+        owlo_i[i] = in.owlo[i];
+        hn1lo_i[i] = in.hn1lo[i];
+        whn1lo_i[i] = in.whn1lo[i];
+    }
     const float* sinx = B.trig + in.trig_off;
     const float* cosx = sinx + nx;
     float2* hist = B.hist + in.hist_off;
@@ -117,7 +126,7 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
                 fp[m] = f2{ft[2 * m], ft[2 * m + 1]};
             });
             const CellOut<float> co = collide_cell_pairs<VS, N, true>(
-                t, 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
+                t, ow_i, owlo_i, hn1lo_i, whn1lo_i, 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
                 [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
             static_for<0, Q / 2>([&](auto mc) {
                 constexpr int m = decltype(mc)::value;

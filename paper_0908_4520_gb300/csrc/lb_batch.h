@@ -26,6 +26,9 @@ struct BatchInst {
     float pad;
     double u0;            // shear-wave amplitude
     double dt;
+    // relaxation tables of this omega: omega W_i and the second terms of the exact FP32
+    // conservation identities (see Tab)
+    float ow[kMaxNA], owlo[kMaxNA], hn1lo[kMaxNA], whn1lo[kMaxNA];
 };
 
 struct BatchArgs {

@@ -34,6 +34,14 @@ struct Tab {
     R winv[kMaxQ];            // 1 / w
     R xixy[kMaxQ];            // xi_x xi_y
     R xi2[kMaxQ];             // |xi|^2
+    // relaxation tables of one omega; the `lo` entries (FP32 only, else 0) are the small second
+    // terms that make the FP32 conservation identities exact (fp32_identities.cpp)
+    R ow[kMaxNA];             // omega W_i (the relaxation weight of the per-axis factors)
+    R owlo[kMaxNA];           // second term of omega W_i in the density term (mass)
+    R hn1lo[kMaxNA];          // second term of He_1(a_i) in the x moment
+    R whn1lo[kMaxNA];         // second term of W_i He_1(a_i) in the y moment
+    R oww[kMaxQ];             // omega w_a (sets without product weights)
+    R mass_lo;                // sets without product weights: mass residual, relaxed with the rest velocity
     R sc[kMaxQ];              // 16-bit storage: deviation = stored * w S
     R scinv[kMaxQ];           // 16-bit storage: stored = deviation / (w S)
 };

@@ -15,6 +15,7 @@ struct VelocitySetInfo {
     lb_quadrature quad = LB_D2Q16_GH;
     int q = 0, na = 0, halo = 0, degree = 0;
     bool on_lattice = false;
+    bool product_weights = false;   // w_a = W[ix] W[iy] (the collision's per-axis factorisation)
     double c = 0.0;                 // lattice scale (on-lattice)
     std::vector<double> axis;       // distinct component values a_i
     std::vector<double> axis_w;     // 1-D Gauss-Hermite weights (product sets)
@@ -46,6 +47,10 @@ inline double snap_unit(double v) {
     const double q = std::fabs(v) >= 1.0 ? 8388608.0 : 16777216.0;
     return std::nearbyint(v * q) / q;
 }
+
+// The FP32 relaxation tables of one omega with the small second terms that make the
+// discrete conservation identities exact (fp32_identities.cpp).
+void fp32_relax_identities(const VelocitySetInfo& vs, float omega, lbk::Tab<float>& t);
 
 // Kernel tables of a velocity set (FP64 on the host, rounded once to R):
 // axis nodes, He_k(a_i)/k!, Lax-Wendroff weights for Courant numbers a_i dt/dx,
@@ -98,6 +103,22 @@ void build_tab(const VelocitySetInfo& vs, double dt, double dx, double scale, lb
         const double p2 = pow2_near(vs.w[a] * scale);
         t.sc[a] = (R)p2;
         t.scinv[a] = (R)(1.0 / p2);
+    }
+}
+
+// The relaxation tables of one omega (the value the kernels receive): omega W_i, omega w_a
+// and, in FP32, the small second terms that make the conservation identities exact.
+template <class R>
+void build_relax(const VelocitySetInfo& vs, R omega, lbk::Tab<R>& t) {
+    if constexpr (std::is_same<R, float>::value) {
+        fp32_relax_identities(vs, omega, t);
+    } else {
+        for (int i = 0; i < vs.na; ++i) {
+            t.ow[i] = omega * t.wm[i];
+            t.owlo[i] = t.hn1lo[i] = t.whn1lo[i] = R(0);
+        }
+        for (int a = 0; a < vs.q; ++a) t.oww[a] = omega * t.w[a];
+        t.mass_lo = R(0);
     }
 }
 

@@ -810,6 +810,9 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
 #pragma unroll
             for (int ky = 1; ky <= N; ++ky)
                 QY[j][ky] = vmul(vsplat<T>(VS::kProductWeights ? t.whn[j][ky] : t.hn[j][ky]), cy[ky]);
+            // FP32: the first-order factor's small second term (exact momentum identity)
+            if constexpr (std::is_same<R, float>::value)
+                QY[j][1] = vfma(vsplat<T>(VS::kProductWeights ? t.whn1lo[j] : t.hn1lo[j]), cy[1], QY[j][1]);
         }
         const T om1 = vsplat<T>(R(1) - omega);
         static_for<0, NA>([&](auto ic) {
@@ -821,12 +824,17 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
                 T sacc = ky == 0 ? zero : vsplat<T>(R(1));
 #pragma unroll
                 for (int kx = 1; kx <= N - ky; ++kx) sacc = vfma(cx[kx], vsplat<T>(t.hn[I][kx]), sacc);
+                if constexpr (std::is_same<R, float>::value) {
+                    if (ky == 0) sacc = vfma(cx[1], vsplat<T>(t.hn1lo[I]), sacc);
+                }
                 px[ky] = sacc;
             }
             if constexpr (VS::kProductWeights) {
-                const T ow = vsplat<T>(omega * t.wm[I]);
+                const T ow = vsplat<T>(t.ow[I]);
                 T PX[N + 1];
-                PX[0] = vmul(ow, vfma(rho, px[0], drho));
+                const T s0 = vfma(rho, px[0], drho);
+                PX[0] = vmul(ow, s0);
+                if constexpr (std::is_same<R, float>::value) PX[0] = vfma(vsplat<T>(t.owlo[I]), s0, PX[0]);
                 const T owr = vmul(ow, rho);
 #pragma unroll
                 for (int ky = 1; ky <= N; ++ky) PX[ky] = vmul(owr, px[ky]);
@@ -849,7 +857,10 @@ __device__ __forceinline__ CellOut<T> collide_cell(const Tab<R>& t, R rho0, R om
                         T sacc = px[0];
 #pragma unroll
                         for (int ky = 1; ky <= N; ++ky) sacc = vfma(px[ky], QY[iy][ky], sacc);
-                        const T od = vmul(vsplat<T>(omega * t.w[a]), vfma(rho, sacc, drho));
+                        T od = vmul(vsplat<T>(t.oww[a]), vfma(rho, sacc, drho));
+                        if constexpr (std::is_same<R, float>::value && VS::kOnLattice) {
+                            if constexpr (VS::ex(a) == 0 && VS::ey(a) == 0) od = vfma(vsplat<T>(t.mass_lo), drho, od);
+                        }
                         T& fa = f(ac);
                         fa = vfma(fa, om1, od);
                     }
@@ -877,10 +888,14 @@ struct PairCollision {
     static constexpr bool value = VS::kProductWeights && !VS::kOnLattice && VS::NA % 2 == 0;
 };
 
+// ow, owlo, hn1lo, whn1lo: the relaxation tables of omega (Tab), the handle's own or, in a
+// batch, the instance's.
 template <class VS, int N, bool COLLIDE, class F>
-__device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t, float rho0, float omega,
-                                                             float sigma_fac, int isothermal, bool diag,
-                                                             bool forced, float gf, float tau, float hdt, F&& fpair) {
+__device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t, const float* ow_t, const float* owlo_t,
+                                                             const float* hn1lo_t, const float* whn1lo_t,
+                                                             float rho0, float omega, float sigma_fac, int isothermal,
+                                                             bool diag, bool forced, float gf, float tau, float hdt,
+                                                             F&& fpair) {
     using R = float;
     constexpr int NA = VS::NA, NP = VS::Q / 2, NJ = NA / 2;
     const f2 z2 = f2{0.f, 0.f};
@@ -981,6 +996,8 @@ __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t
 #pragma unroll
             for (int ky = 1; ky <= N; ++ky)
                 QYp[j][ky] = vmul(f2{t.whn[2 * j][ky], t.whn[2 * j + 1][ky]}, vsplat<f2>(cy[ky]));
+            // the first-order factor's small second term (exact momentum identity)
+            QYp[j][1] = vfma(f2{whn1lo_t[2 * j], whn1lo_t[2 * j + 1]}, vsplat<f2>(cy[1]), QYp[j][1]);
         }
         const f2 om1 = vsplat<f2>(1.f - omega);
         static_for<0, NA>([&](auto ic) {
@@ -993,10 +1010,12 @@ __device__ __forceinline__ CellOut<float> collide_cell_pairs(const Tab<float>& t
                     R sacc = ky == 0 ? 0.f : 1.f;
 #pragma unroll
                     for (int kx = 1; kx <= N - ky; ++kx) sacc = fmaf(cx[kx], t.hn[I][kx], sacc);
+                    if (ky == 0) sacc = fmaf(cx[1], hn1lo_t[I], sacc);
                     px[ky] = sacc;
                 }
-                const R ow = omega * t.wm[I];
-                PX[0] = __fmul_rn(ow, fmaf(rho, px[0], drho));
+                const R ow = ow_t[I];
+                const R s0 = fmaf(rho, px[0], drho);
+                PX[0] = fmaf(owlo_t[I], s0, __fmul_rn(ow, s0));
                 const R owr = __fmul_rn(ow, rho);
 #pragma unroll
                 for (int ky = 1; ky <= N; ++ky) PX[ky] = __fmul_rn(owr, px[ky]);
@@ -1066,7 +1085,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
             fp[m] = f2{ft[2 * m], ft[2 * m + 1]};
         });
         co = collide_cell_pairs<VS, N, STEP>(
-            A.tab, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
+            A.tab, A.tab.ow, A.tab.owlo, A.tab.hn1lo, A.tab.whn1lo, A.rho0, A.omega, A.sigma_fac, A.isothermal, diag || KIND == kMoments, forced, gf, A.tau,
             A.hdt, [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
         static_for<0, NP>([&](auto mc) {
             constexpr int m = decltype(mc)::value;

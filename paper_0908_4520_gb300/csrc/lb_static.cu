@@ -26,6 +26,7 @@
 #include "lb_host.h"
 
 static __device__ __align__(256) unsigned char lb_static_scratch[LB_STATIC_SCRATCH_BYTES];
+static_assert(sizeof(lbk::BatchInst) <= 256, "the instance descriptor fills the first 256 bytes of the scratch");
 
 namespace {
 
@@ -178,6 +179,14 @@ lb_status lb_solve_static(const lb_instance_desc* d, lb_precision precision, lb_
     const double tau = kn_convention == LB_KN_LAMBDA ? d->kn * std::sqrt(2.0 / M_PI) : d->kn;
     const double omega = lbh::snap_unit(dt / (tau + 0.5 * dt));
     in.omega = (float)omega;
+    {
+        lbk::Tab<float> rt = g_tab[si];
+        lbh::build_relax<float>(g_sets[si], in.omega, rt);
+        std::memcpy(in.ow, rt.ow, sizeof(in.ow));
+        std::memcpy(in.owlo, rt.owlo, sizeof(in.owlo));
+        std::memcpy(in.hn1lo, rt.hn1lo, sizeof(in.hn1lo));
+        std::memcpy(in.whn1lo, rt.whn1lo, sizeof(in.whn1lo));
+    }
     in.sigma_fac = (float)(1.0 - 0.5 * omega);
     in.scale = (float)lbh::pow2_near(std::max(2.0 * std::fabs(d->u0), 1e-6));
     in.stop_ratio2 = (float)(d->stop_ratio * d->stop_ratio);

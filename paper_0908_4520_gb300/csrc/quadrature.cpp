@@ -258,6 +258,7 @@ void fill_indices(VelocitySetInfo& vs) {
     vs.na = VS::NA;
     vs.halo = VS::kHalo;
     vs.on_lattice = VS::kOnLattice;
+    vs.product_weights = VS::kProductWeights;
     vs.ix.resize(VS::Q);
     vs.iy.resize(VS::Q);
     vs.ex.resize(VS::Q);

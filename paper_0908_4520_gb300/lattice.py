@@ -15,7 +15,7 @@ class Lattice:
     stream: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
     or None for a stream the handle creates.
     step_kernel: "auto", "plain" (coalesced loads), "tma" (TMA-staged) or "tma_store" (TMA-staged
-    with TMA tensor stores; FP32 Lax-Wendroff sets up to 36 velocities); same results.
+    with TMA tensor stores; FP32 Lax-Wendroff sets up to 36 velocities, nx a multiple of 4); same results.
     force_amp, force_freq: body force g_y = force_amp sin(x_i) cos(force_freq t) driving the
     standing shear wave (0: free decay).
     n_eq: Hermite order N of the equilibrium, 1..4 (1: f^eq = w rho (1 + xi.u)).

@@ -72,6 +72,24 @@ def window(P, t):
     return min(5.0 * P.tau, t[-1] / 4.0)
 
 
+def monotone_window(d, t0, floor=1e-4):
+    """The oracle's A(n) keeps the sign of A(0) from t0 until it falls below the fit floor."""
+    t, A = d[:, 0], d[:, 4]
+    sel = t >= t0
+    live = np.abs(A) >= floor * abs(A[0])
+    stop = np.argmin(live[sel]) if not np.all(live[sel]) else np.sum(sel)
+    return bool(np.all(np.sign(A[sel][:stop]) == np.sign(A[0])))
+
+
+def test_fit_window_rule():
+    """The rule that decides where a decay rate is compared, on the oracle's own histories:
+    the small-Kn wave decays monotonically, the Kn ~ 6 wave oscillates through zero."""
+    P, d, _ = oracle_run("D2Q64-GH", 4, _KN[0])
+    assert monotone_window(d, window(P, d[:, 0]))
+    P, d, _ = oracle_run("D2Q64-GH", 4, _KN[-1])
+    assert not monotone_window(d, window(P, d[:, 0]))
+
+
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 @pytest.mark.parametrize("quad,N,kn", CASES)
 def test_sixteen_bit_storage_against_oracle(quad, N, kn, prec):
@@ -87,11 +105,14 @@ def test_sixteen_bit_storage_against_oracle(quad, N, kn, prec):
     P, d, uy_o = oracle_run(quad, N, kn)
     s = sigma(P, prec)
     f32_allow = STEPS * omega * 2.0 ** -24
-    # decay rate: the same fit on both histories
+    # decay rate: the same fit on both histories, where it is defined (the oracle's A(n) keeps
+    # its sign over the fit window; at large Kn it oscillates through zero and only the
+    # amplitude history below is compared)
     t0 = window(P, d[:, 0])
-    r_gpu = oracle.decay_fit(rec["t"], rec["amp"], t0)
-    r_ora = oracle.decay_fit(d[:, 0], d[:, 4], t0)
-    assert abs(r_gpu / r_ora - 1.0) < 1e-3, (r_gpu, r_ora)
+    if monotone_window(d, t0):
+        r_gpu = oracle.decay_fit(rec["t"], rec["amp"], t0)
+        r_ora = oracle.decay_fit(d[:, 0], d[:, 4], t0)
+        assert abs(r_gpu / r_ora - 1.0) < 1e-3, (r_gpu, r_ora)
     # amplitude history
     amp_err = np.max(np.abs(rec["amp"] - d[:, 4])) / U0
     amp_bound = 3.0 * math.sqrt(2.0 * STEPS / (NX * NY)) * s + f32_allow
