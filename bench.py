@@ -158,6 +158,8 @@ def workload_name(args):
 
 def kernel_label(args, tma):
     st = {"f32": "float", "f64": "double", "f16": "__half", "bf16": "__nv_bfloat16"}[args.precision]
+    if tma == 2:
+        return f"lb_tma_step_kernel<{args.quad}, {args.n_eq}, {st}, upwind=0, kStep, store_staged=1>"
     if tma:
         return f"lb_tma_step_kernel<{args.quad}, {args.n_eq}, {st}>"
     return f"lb_fused_kernel<{args.quad}, {args.n_eq}, {st}, kStep>"
@@ -317,7 +319,7 @@ def run_gpu(args):
         if quad == args.quad:
             main_ms = ms
             main_L = L
-            main_tma = bool(info["tma_staged"])
+            main_tma = int(info["tma_staged"])
         else:
             L.close()
 
