@@ -121,8 +121,9 @@ typedef struct {
     int diag_capacity;         /* records kept in the device ring (default 65536) */
     double storage_scale;      /* 16-bit scale S (rounded to a power of two); 0 = 2 x the initial amplitude */
     int step_kernel;           /* 0: automatic; 1: plain-load step kernel; 2: TMA-staged step kernel;
-                                  3: TMA-staged with TMA tensor stores of each tile (FP32
-                                  Lax-Wendroff sets up to 36 velocities, nx a multiple of 4)
+                                  3: TMA-staged with TMA tensor stores of each tile
+                                  (Lax-Wendroff sets: FP32 up to 36 velocities, 16-bit all; nx
+                                  a multiple of 4 for FP32, of 8 for 16-bit)
                                   (LB_ERR_UNSUPPORTED if not built for the set or storage).  All
                                   give bitwise-identical populations. */
     void *stream;              /* cudaStream_t to run on; NULL = a stream the handle creates */
@@ -228,6 +229,27 @@ lb_status lb_fit_decay(lb_handle *h, double t_start, double floor_rel, double *r
 
 /* Wait for the handle's work; reports device-side errors. */
 lb_status lb_synchronize(lb_handle *h);
+
+/* Slab decomposition of one periodic grid over several lattices (one per GPU, or several
+ * on one GPU): each lattice holds a band of rows of the grid, and its streaming (Sec. 2.3:
+ * exact shift by e_a, or the Lax-Wendroff stencil) reads gy rows beyond its own on either
+ * side (gy = info.halo rows: 1 for Lax-Wendroff, max|e_y| for the exact shift, 2 for
+ * second-order upwind).  Between two levels the caller fills those ghost rows with the
+ * neighbours' boundary rows: pack side 0 (rows 0..gy-1) and side 1 (rows ny-gy..ny-1) of
+ * this lattice's state into device buffers, move them to the lower and upper neighbour,
+ * and unpack what arrives into side 0 (ghost rows -gy..-1) and side 1 (ghost rows
+ * ny..ny+gy-1).  The library's own kernels fill the ghost rows with the lattice's own
+ * periodic images; an exchange after init and after every lb_step(h, 1) overwrites them,
+ * so a lattice stepped one level at a time between exchanges advances its band of the
+ * whole grid.  Both calls act on the state the next lb_step reads, are enqueued on the
+ * handle's stream (asynchronous; order other streams with events), and copy whole padded
+ * rows of every velocity plane.  dst / src: device buffers of lb_halo_bytes bytes, owned by
+ * the caller.  LB_ERR_STATE before init; LB_ERR_ARG for a side other than 0, 1 or a NULL
+ * buffer.  The paper has no slab decomposition; this is the data-parallel split of its
+ * grid. */
+lb_status lb_halo_bytes(const lb_handle *h, size_t *bytes);
+lb_status lb_halo_pack(lb_handle *h, int side, void *dst);
+lb_status lb_halo_unpack(lb_handle *h, int side, const void *src);
 
 lb_status lb_get_info(const lb_handle *h, lb_info_t *out);
 

@@ -127,6 +127,9 @@ def _load() -> ctypes.CDLL:
         "lb_diagnostics": (ctypes.c_int, [H, ctypes.POINTER(lb_diag), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "lb_diagnostics_at": (ctypes.c_int, [H, ctypes.c_longlong, ctypes.POINTER(lb_diag)]),
         "lb_synchronize": (ctypes.c_int, [H]),
+        "lb_halo_bytes": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_size_t)]),
+        "lb_halo_pack": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_void_p]),
+        "lb_halo_unpack": (ctypes.c_int, [H, ctypes.c_int, ctypes.c_void_p]),
         "lb_get_info": (ctypes.c_int, [H, ctypes.POINTER(lb_info_t)]),
         "lb_kernel_launches": (ctypes.c_longlong, [H]),
         "lb_destroy": (ctypes.c_int, [H]),
@@ -189,7 +192,7 @@ EXPORTS = [
     "lb_batch_bytes_in_use", "lb_batch_kernel_launches", "lb_batch_destroy", "lb_batch_last_error",
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
     "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static", "lb_dvm_run",
-    "lb_dvm_run_forced", "lb_diagnostics_at",
+    "lb_dvm_run_forced", "lb_diagnostics_at", "lb_halo_bytes", "lb_halo_pack", "lb_halo_unpack",
 ]
 
 
@@ -277,6 +280,21 @@ def lb_diagnostics_at(h, level: int, out: lb_diag | None = None) -> lb_diag:
 
 def lb_synchronize(h):
     return check(lib.lb_synchronize(h), h)
+
+
+def lb_halo_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    check(lib.lb_halo_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def lb_halo_pack(h, side: int, dst: int):
+    """dst: device pointer (int) of lb_halo_bytes bytes."""
+    return check(lib.lb_halo_pack(h, side, ctypes.c_void_p(dst)), h)
+
+
+def lb_halo_unpack(h, side: int, src: int):
+    return check(lib.lb_halo_unpack(h, side, ctypes.c_void_p(src)), h)
 
 
 def lb_get_info(h) -> lb_info_t:

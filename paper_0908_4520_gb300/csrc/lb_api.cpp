@@ -647,10 +647,11 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         // auto: TMA staging once the grid fills a tile row and every SM gets work
         const bool big = P.nx >= ttw && h->tma_ntiles >= nsm;
         h->use_tma = P.step_kernel >= 2 || (P.step_kernel == 0 && big);
-        // the store-staged kernel (FP32 Lax-Wendroff sets): automatic on the same grids.  Its
-        // stores cover whole 16-byte granules of a row, so nx must be a multiple of 4 (else the
-        // store of the last tile would reach the periodic images past nx)
-        if (h->shape.st && !upwind && P.nx % 4 == 0) {
+        // the store-staged kernel (Lax-Wendroff sets): automatic on the same grids where it is
+        // the faster.  Its stores cover whole 16-byte granules of a row, so nx must be a multiple
+        // of 16 / (bytes per population) (else the store of the last tile would reach the
+        // periodic images past nx)
+        if (h->shape.st && !upwind && P.nx % (int)(16 / storage_bytes(P.precision)) == 0) {
             h->st_ntiles_x = (P.nx + h->shape.st_tw - 1) / h->shape.st_tw;
             h->st_ntiles = h->st_ntiles_x * ((P.ny + h->shape.st_rows - 1) / h->shape.st_rows);
             h->st_grid = std::max(1, std::min(h->st_ntiles, nsm * std::max(1, h->shape.st_occupancy)));
@@ -659,7 +660,7 @@ lb_status lb_create_ex(const lb_params* pin, lb_handle** out) {
         if (P.step_kernel == 3 && !h->use_st) {
             delete h;
             return reject(LB_ERR_UNSUPPORTED,
-                          "no store-staged TMA step kernel for this set, storage, streaming or nx (a multiple of 4)");
+                          "no store-staged TMA step kernel for this set, storage, streaming or nx (a multiple of 16 bytes)");
         }
     } else if (P.step_kernel >= 2) {
         delete h;
@@ -787,6 +788,46 @@ lb_status lb_step(lb_handle* h, int n) {
         if (n == 0) return h->mark_level();
     }
     return LB_OK;
+}
+
+// ---- slab decomposition: the ghost and boundary row blocks of the state the next step reads
+namespace {
+// element offset (in a plane) of the gy rows starting at row r0 (r0 in [-gy, ny + gy - gy])
+long long row_block(const lb_handle* h, int r0) { return (long long)(r0 + h->gy) * h->pitch; }
+
+lb_status halo_copy(lb_handle* h, int side, void* dst, const void* src, bool pack) {
+    if (!h->initialized) return h->fail(LB_ERR_STATE, "init first");
+    if ((side != 0 && side != 1) || (pack ? !dst : !src)) return h->fail(LB_ERR_ARG, "side 0 or 1 and a device buffer");
+    const size_t b = storage_bytes(h->p.precision);
+    const size_t block = (size_t)h->gy * h->pitch * b;   // gy whole padded rows of one plane
+    const size_t plane = (size_t)h->plane * b;
+    char* state = static_cast<char*>(h->buf[h->cur]);
+    // pack: boundary rows 0..gy-1 or ny-gy..ny-1; unpack: ghost rows -gy..-1 or ny..ny+gy-1
+    const int r0 = pack ? (side == 0 ? 0 : h->p.ny - h->gy) : (side == 0 ? -h->gy : h->p.ny);
+    char* rows = state + row_block(h, r0) * (long long)b;
+    const cudaError_t e = pack ? cudaMemcpy2DAsync(dst, block, rows, plane, block, h->vs.q, cudaMemcpyDeviceToDevice,
+                                                   h->stream)
+                               : cudaMemcpy2DAsync(rows, plane, src, block, block, h->vs.q, cudaMemcpyDeviceToDevice,
+                                                   h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, pack ? "halo pack" : "halo unpack");
+    return LB_OK;
+}
+}  // namespace
+
+lb_status lb_halo_bytes(const lb_handle* h, size_t* bytes) {
+    if (!h || !bytes) return LB_ERR_ARG;
+    *bytes = (size_t)h->vs.q * h->gy * h->pitch * storage_bytes(h->p.precision);
+    return LB_OK;
+}
+
+lb_status lb_halo_pack(lb_handle* h, int side, void* dst) {
+    if (!h) return LB_ERR_ARG;
+    return halo_copy(h, side, dst, nullptr, true);
+}
+
+lb_status lb_halo_unpack(lb_handle* h, int side, const void* src) {
+    if (!h) return LB_ERR_ARG;
+    return halo_copy(h, side, nullptr, src, false);
 }
 
 lb_status lb_synchronize(lb_handle* h) {

@@ -422,10 +422,13 @@ struct Pack<float, 2> {
 #define LB_TMA_BAND_SHIFT 4  // band height of the exact-shift sets under LB_TMA_BAND = -1
 #endif
 #ifndef LB_TMA_WIDE_WARPS
-#define LB_TMA_WIDE_WARPS 18  // consumer warps of the store-staged kernel (two per tile row)
+#define LB_TMA_WIDE_WARPS 0  // consumer warps of the store-staged kernel (two per tile row); 0: 18, q = 64: 14
 #endif
 #ifndef LB_TMA_WIDE_SMEM
-#define LB_TMA_WIDE_SMEM (224 * 1024)  // ring + output tile of the store-staged kernel
+// ring + output tile of the store-staged kernel.  D2Q36-GH FP32 at 4096^2 (GLUPS): 224 KB
+// (8 stages) 17.2, 192 KB (6 stages: one tile ahead) 17.5; 9 velocities per stage instead of 6:
+// +0.2 %; 16 / 20 consumer warps instead of 18: 15.0 / 15.9
+#define LB_TMA_WIDE_SMEM (192 * 1024)
 #endif
 #ifndef LB_DIAG_PREFETCH
 // load sin/cos of the diagnostics before the collision: -1 per set (measured at 4096^2 FP32,
@@ -452,22 +455,23 @@ struct Cfg {
 // UPW: second-order upwind streaming of a Lax-Wendroff set (one cell per lane): lanes
 // 0, 1 and 30, 31 compute the y pass of the two columns on either side of the 28 cells
 // that lanes 2..29 own, and the box carries two extra rows above and below.
-// WIDE: the store-staged variant of the Lax-Wendroff kernel (FP32, one cell per lane, halo
-// lanes): two warps share a tile row (30 cells each, 60 per row, 240 bytes: a multiple of
-// the 16-byte TMA granule), the consumer warps write the relaxed populations of the tile
-// into a shared-memory output tile, and the producer warp writes it to HBM with one TMA
-// tensor store per tile (cp.async.bulk.tensor, shared -> global), so no thread issues
-// per-velocity global stores.
+// WIDE: the store-staged variant of the Lax-Wendroff kernel (one cell per lane, halo
+// lanes): two warps share a tile row (FP32: 30 cells each, 60 per row, 240 bytes; 16-bit:
+// 28 cells each - lanes 30, 31 idle - 56 per row, 112 bytes: whole 16-byte TMA granules),
+// the consumer warps write the relaxed populations of the tile (16-bit: stochastically
+// rounded) into a shared-memory output tile, and the producer warp writes it to HBM with
+// one TMA tensor store per tile (cp.async.bulk.tensor, shared -> global), so no thread
+// issues per-velocity global stores and every DRAM sector of the tile is written whole.
 template <class VS, class S, bool UPW = false, bool WIDE = false>
 struct TmaCfg {
     static constexpr bool LW = !VS::kOnLattice;
     static constexpr int V = cells_per_lane<VS, S, LB_TMA_V>();
     static_assert(!UPW || (LW && V == 1), "upwind TMA staging: Lax-Wendroff sets, one cell per lane");
-    static_assert(!WIDE || (LW && V == 1 && !UPW && sizeof(S) == 4), "store staging: FP32 Lax-Wendroff sets");
+    static_assert(!WIDE || (LW && V == 1 && !UPW && sizeof(S) <= 4), "store staging: 32/16-bit Lax-Wendroff sets");
     // consumer warps (+ one producer warp); the register cap follows from the count
     // (exact shift at 4096^2 FP32, 11 / 13 rows, GLUPS: D2Q37 18.3 / 16.8, D2Q25 21.3 / 22.3,
     // D2Q21 25.4 / 27.7, D2Q17 41.6 / 42.1, D2Q16 44.7 / 45.1, D2Q9 68.6 / 72.6)
-    static constexpr int CW = WIDE ? LB_TMA_WIDE_WARPS
+    static constexpr int CW = WIDE ? (LB_TMA_WIDE_WARPS > 0 ? LB_TMA_WIDE_WARPS : (VS::Q > 40 ? 14 : 18))
                                    : (LB_TMA_ROWS > 0 ? LB_TMA_ROWS : (LW ? (VS::Q > 40 ? 15 : 19) : (VS::Q > 30 ? 11 : 13)));
     static constexpr int WPR = WIDE ? 2 : 1;            // consumer warps per tile row
     static constexpr int ROWS = CW / WPR;               // lattice rows of a tile
@@ -479,9 +483,12 @@ struct TmaCfg {
     // 16-bit 12.1 / 15.9 / 14.4; D2Q64 FP32 5.38 / 4.95 / 4.97; D2Q64 16-bit 4.37 / 6.40 / 6.28.
     static constexpr bool FP32_Q64 = sizeof(S) == 4 && VS::Q > 40;
     static constexpr bool HALO = WIDE || (!UPW && LW && V == 1 && (LB_TMA_HALO > 0 || (LB_TMA_HALO < 0 && !FP32_Q64)));
+    // (store-staged: no per-tile barrier; without per-velocity stores the warps stay together,
+    // and the barrier cost 5 %: 16.3 against 17.2 GLUPS for D2Q36-GH FP32 at 4096^2)
     static constexpr bool TILE_SYNC =
-        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && (HALO || UPW) && sizeof(S) == 4 && VS::Q == 36);
-    static constexpr int WCELLS = UPW ? 28 : (HALO ? 30 : TW);  // cells a warp produces
+        LB_TMA_TILE_SYNC > 0 || (LB_TMA_TILE_SYNC < 0 && !WIDE && (HALO || UPW) && sizeof(S) == 4 && VS::Q == 36);
+    // cells a warp produces (store-staged 16-bit: 28, so that a tile row is 7 granules)
+    static constexpr int WCELLS = UPW ? 28 : (WIDE && sizeof(S) == 2 ? 28 : (HALO ? 30 : TW));
     static constexpr int TWO = WPR * WCELLS;            // cells a tile row produces
     static constexpr int GX = UPW ? 2 : 1;              // stencil reach (columns and rows) of the box
     static constexpr int BAND = LB_TMA_BAND >= 0 ? LB_TMA_BAND : (LW ? 0 : LB_TMA_BAND_SHIFT);  // tile order
@@ -572,10 +579,12 @@ struct Lane {
 // TMA-staged Lax-Wendroff with one cell per lane: the warp's edge lanes are halo lanes
 // (columns x0 - 1 and x0 + 30), whose y-pass only feeds their neighbours' x-pass, so no
 // lane reads an extra column; lanes 1..30 own cells x0 .. x0 + 29.
-__device__ __forceinline__ Lane halo_lane_geometry(int lane, int x0, int tile_start, int nx) {
+// (own: the number of cells the warp owns, lanes 1..own; 30, or 28 for the store-staged
+// 16-bit kernel, whose lanes 30 and 31 are idle)
+__device__ __forceinline__ Lane halo_lane_geometry(int lane, int x0, int tile_start, int nx, int own = 30) {
     Lane g;
     g.x = x0 - 1 + lane;
-    g.own = lane >= 1 && lane <= 30 && g.x < nx && g.x >= tile_start;
+    g.own = lane >= 1 && lane <= own && g.x < nx && g.x >= tile_start;
     g.xl = g.x;
     return g;
 }
@@ -1044,7 +1053,7 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
                                               const Lane& g, bool diag, R (&acc)[6], int lane, long long lvl,
                                               R gt, S* out = nullptr) {
     constexpr int Q = VS::Q;
-    static_assert(OSTRIDE == 0 || (V == 1 && sizeof(S) == 4), "output tile: FP32, one cell per lane");
+    static_assert(OSTRIDE == 0 || V == 1, "output tile: one cell per lane");
     // body force g_y(x_i, t_n) = gt sin(x_i), gt = A_f cos(phi t_n) (driven standing wave, Sec. 4);
     // compiled out of the unforced step kernels
     constexpr bool STEP = (KIND == kStep || KIND == kStepForced);
@@ -1118,9 +1127,17 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     }
     if constexpr (STEP && OSTRIDE > 0) {
         if (g.own) {
+            // the same stochastic rounding stream as the global stores below (same bits)
+            uint32_t r0 = 0;
+            if constexpr (Is16<S>::value) r0 = sr_seed(lvl, (long long)y * A.nx + g.x);
             static_for<0, Q>([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                out[a * OSTRIDE] = lane_get<0>(ft[a]);
+                if constexpr (Is16<S>::value) {
+                    r0 = sr_next(r0);
+                    out[a * OSTRIDE] = to_storage<S, R>(lane_get<0>(ft[a]), store_scale<S, R>(A.tab, a), r0);
+                } else {
+                    out[a * OSTRIDE] = lane_get<0>(ft[a]);
+                }
             });
             if (g.x < kGhostX || g.x + V > A.nx - kGhostX || y < A.gy || y >= A.ny - A.gy)
                 rim_images_tile<S, R>(A, dst, out, OSTRIDE, Q, g.x, y);
@@ -1632,7 +1649,7 @@ __global__ void __maxnreg__((TmaCfg<VS, S, UPW, WIDE>::MAXREG))
             const int x0 = (!WIDE && tx == A.ntiles_x - 1) ? A.x0_last : tile_start;
             const int y = ty * ROWS + trow;
             const Lane g = UPW      ? upwind_lane_geometry(lane, x0, tile_start, A.nx)
-                           : C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx)
+                           : C::HALO ? halo_lane_geometry(lane, x0, tile_start, A.nx, C::WCELLS)
                                      : lane_geometry<V>(lane, x0, tile_start, A.nx);
             using T = typename Pack<R, V>::T;
             T ft[Q];
@@ -1835,9 +1852,9 @@ cudaError_t launch_typed(const Launch& L) {
     // for FP32 storage
     constexpr bool kUpw = !VS::kOnLattice && !Is16<S>::value;
     constexpr bool kUpwTma = kUpw && kTma && std::is_same<S, float>::value;
-    // store-staged TMA kernel: FP32 Lax-Wendroff sets up to 36 velocities (the output tile of
-    // a 64-velocity set leaves too little shared memory for the ring)
-    constexpr bool kStore = kTma && !VS::kOnLattice && std::is_same<S, float>::value && VS::Q <= 40;
+    // store-staged TMA kernel: Lax-Wendroff sets, FP32 up to 36 velocities (the FP32 output
+    // tile of a 64-velocity set leaves too little shared memory for the ring), 16-bit all
+    constexpr bool kStore = kTma && !VS::kOnLattice && ((std::is_same<S, float>::value && VS::Q <= 40) || Is16<S>::value);
     if (L.kind == kQueryShape) {
         Shape* sh = static_cast<Shape*>(const_cast<void*>(L.args));
         sh->V = C::V;
@@ -1898,7 +1915,7 @@ cudaError_t launch_typed(const Launch& L) {
                     sh->st_box_h = TS::BH;
                     // measured at 4096^2 (GLUPS, TMA-staged / store-staged): D2Q36-GH N = 3 13.8 /
                     // 16.2, N = 2 11.4 / 16.9, N = 1 9.8 / 18.1; D2Q16-GH N = 2 38.2 / 31.5
-                    sh->st_auto = VS::Q > 16 ? 1 : 0;
+                    sh->st_auto = (sizeof(S) == 4 && VS::Q > 16) ? 1 : 0;
                 }
             }
         }

@@ -15,7 +15,8 @@ class Lattice:
     stream: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
     or None for a stream the handle creates.
     step_kernel: "auto", "plain" (coalesced loads), "tma" (TMA-staged) or "tma_store" (TMA-staged
-    with TMA tensor stores; FP32 Lax-Wendroff sets up to 36 velocities, nx a multiple of 4); same results.
+    with TMA tensor stores; Lax-Wendroff sets, FP32 up to 36 velocities or 16-bit, nx a whole
+    number of 16-byte granules); same results.
     force_amp, force_freq: body force g_y = force_amp sin(x_i) cos(force_freq t) driving the
     standing shear wave (0: free decay).
     n_eq: Hermite order N of the equilibrium, 1..4 (1: f^eq = w rho (1 + xi.u)).
@@ -99,6 +100,16 @@ class Lattice:
         inf = capi.lb_get_info(self.h)
         n = int(inf.records) if max_records is None else max_records
         return capi.lb_diagnostics(self.h, max(n, 1))
+
+    # -- slab decomposition (see slab.py): buffers are device tensors of halo_bytes() bytes
+    def halo_bytes(self) -> int:
+        return capi.lb_halo_bytes(self.h)
+
+    def halo_pack(self, side: int, buf):
+        capi.lb_halo_pack(self.h, side, buf.data_ptr())
+
+    def halo_unpack(self, side: int, buf):
+        capi.lb_halo_unpack(self.h, side, buf.data_ptr())
 
     def fit_decay(self, t_start: float, floor_rel: float = 1e-4):
         """(rate, npoints, shear/amplitude ratio) from the FP64 fit of the library."""

@@ -290,15 +290,19 @@ def test_diagnostics_at_reads_each_level_while_the_next_runs():
         capi.lb_diagnostics_at(L.h, 75)  # not produced yet
 
 
-@pytest.mark.parametrize("quad,N,nx,ny", [("D2Q36-GH", 3, 256, 40), ("D2Q36-GH", 3, 132, 17), ("D2Q16-GH", 2, 64, 8),
-                                          ("D2Q16-GH", 4, 36, 20), ("D2Q36-GH", 2, 64, 9), ("D2Q36-GH", 1, 124, 10)])
-def test_store_staged_and_plain_kernels_are_bitwise_equal(quad, N, nx, ny):
-    """The TMA-staged kernel with TMA tensor stores of each tile (60-column tiles, clipped at
-    nx and ny; the periodic images in the rim written by the boundary lanes) gives the
-    plain-load kernel's populations bit for bit (nx a multiple of 4, as it requires)."""
+@pytest.mark.parametrize("quad,N,prec,nx,ny", [("D2Q36-GH", 3, "f32", 256, 40), ("D2Q36-GH", 3, "f32", 132, 17),
+                                               ("D2Q16-GH", 2, "f32", 64, 8), ("D2Q16-GH", 4, "f32", 36, 20),
+                                               ("D2Q36-GH", 2, "f32", 64, 9), ("D2Q36-GH", 1, "f32", 124, 10),
+                                               ("D2Q64-GH", 4, "bf16", 200, 30), ("D2Q64-GH", 4, "f16", 56, 7),
+                                               ("D2Q36-GH", 3, "f16", 136, 19), ("D2Q16-GH", 2, "bf16", 40, 9)])
+def test_store_staged_and_plain_kernels_are_bitwise_equal(quad, N, prec, nx, ny):
+    """The TMA-staged kernel with TMA tensor stores of each tile (FP32: 60-column tiles,
+    16-bit: 56-column tiles with the same stochastic rounding; clipped at nx and ny; the
+    periodic images in the rim written by the boundary lanes) gives the plain-load kernel's
+    populations bit for bit (nx a whole number of 16-byte granules, as it requires)."""
     Lattice, capi = lib()
-    a = Lattice(quad, N, nx, ny, 0.1, step_kernel="tma_store").init_shear_wave(1e-3, 1e-3)
-    b = Lattice(quad, N, nx, ny, 0.1, step_kernel="plain").init_shear_wave(1e-3, 1e-3)
+    a = Lattice(quad, N, nx, ny, 0.1, precision=prec, step_kernel="tma_store").init_shear_wave(1e-3, 1e-3)
+    b = Lattice(quad, N, nx, ny, 0.1, precision=prec, step_kernel="plain").init_shear_wave(1e-3, 1e-3)
     assert a.info["tma_staged"] == 2 and b.info["tma_staged"] == 0
     a.step(37)
     b.step(37)
@@ -309,11 +313,12 @@ def test_store_staged_and_plain_kernels_are_bitwise_equal(quad, N, nx, ny):
     b.close()
 
 
-def test_store_staged_kernel_needs_nx_multiple_of_four():
+def test_store_staged_kernel_needs_whole_granules():
     Lattice, capi = lib()
-    with pytest.raises(capi.LBError) as e:
-        Lattice("D2Q36-GH", 3, 130, 17, 0.1, step_kernel="tma_store")
-    assert e.value.status == capi.LB_ERR_UNSUPPORTED
+    for prec, nx in (("f32", 130), ("f16", 132)):
+        with pytest.raises(capi.LBError) as e:
+            Lattice("D2Q36-GH", 3, nx, 17, 0.1, precision=prec, step_kernel="tma_store")
+        assert e.value.status == capi.LB_ERR_UNSUPPORTED
     # the automatic choice falls back to the TMA-staged kernel with plain stores
     L = Lattice("D2Q36-GH", 3, 4094, 64, 0.1)
     assert L.info["tma_staged"] == 1
