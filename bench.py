@@ -192,12 +192,13 @@ def dvm_crosscheck(capi, Lattice, args, n=256, t_end=6.0):
 
 
 def time_quadrature(torch, Lattice, quad, nx, ny, steps, warmup, kn, n_eq=3, precision="f32",
-                    scheme="second_order", streaming="lax_wendroff"):
+                    scheme="second_order", streaming="lax_wendroff", step_kernel="auto"):
     stream = torch.cuda.Stream()
     if not quad.endswith("-GH"):
         streaming = "lax_wendroff"  # on-lattice sets stream by the exact shift
+        step_kernel = "auto" if step_kernel == "tma_store" else step_kernel
     L = Lattice(quad, n_eq, nx, ny, kn, precision=precision, stream=stream.cuda_stream, scheme=scheme,
-                streaming=streaming)
+                streaming=streaming, step_kernel=step_kernel)
     L.init_shear_wave(1e-3, 1e-3)
     L.step(warmup)
     L.synchronize()
@@ -287,7 +288,8 @@ def run_gpu(args):
         if not quad:
             continue
         L, stream, ev0, ev1, n0 = time_quadrature(torch, Lattice, quad, nx, ny, args.steps, args.warmup, args.kn,
-                                                  args.n_eq, args.precision, args.scheme, args.streaming)
+                                                  args.n_eq, args.precision, args.scheme, args.streaming,
+                                                  args.step_kernel)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -623,6 +625,29 @@ def run_batch(args):
     b.close()
 
 
+def issue_roof(key, mlups):
+    """The instruction-issue roofline of a kernel whose warp instructions per cell were counted
+    by ncu (profiles/ncu_instructions.json, valid while the kernel sources' code is unchanged):
+    every SM issuing 4 warp instructions per cycle at the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_instructions.json")) as fh:
+            ent = json.load(fh).get(key)
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return None
+    if not ent or ent.get("kernel_digest") != kernel_digest():
+        return None
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * mhz * 1e6 / ent["warp_instructions_per_cell"] / 1e6
+    return {"bound": "alu", "achieved": mlups, "peak": round(peak, 1), "unit": "MLUPS",
+            "frac": round(mlups / peak, 4), "warp_instructions_per_cell": round(ent["warp_instructions_per_cell"], 2),
+            "peak_source": f"{sms} SMs x 4 warp instructions per cycle x {mhz:.0f} MHz / instructions per cell "
+                           f"({ent['profile']})"}
+
+
 def run_precision(args):
     """Precision workload: D2Q64-GH, N = 4, 2048^2, U0 = 1e-4, 16-bit deviation storage
     (stochastic rounding) and FP32: MLUPS, and every run's error against the FP64 oracle
@@ -695,6 +720,9 @@ def run_precision(args):
         if prec != "f32":
             rel = [abs(a / b - 1) for a, b in zip(r["rate"], out["f32"]["rate"])]
             res[prec]["max_decay_rate_rel_err_vs_f32"] = float("%.3g" % max(rel))
+        roof = issue_roof(f"D2Q64-GH/4/{prec}", res[prec]["mlups"])
+        if roof:
+            res[prec]["roofline_issue"] = roof
     _common(args, "MLUPS of 16-bit deviation storage (D2Q64-GH, N=4) and its errors vs the FP64 oracle",
             res["f16"]["mlups"], "MLUPS", {
                 "steps": steps, "warmup": args.warmup,
@@ -935,6 +963,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "tma_store"],
+                    help="step kernel of the timed lattice (auto: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--check-steps", type=int, default=2000,
                     help="levels of the error check against the oracle (0 = no check)")
