@@ -573,7 +573,7 @@ def run_batch(args):
     need = sum(2 * qmap[d["quadrature"]] * d["nx"] * d["ny"] * 4 + 8 * (d["max_steps"] + 2) + 8 * d["nx"] + 1024
                for d in inst)
     b = Batch("f32", budget_bytes=int(need * 1.2) + (64 << 20), threads=tuned["threads"],
-              smem_bytes=tuned["smem_bytes"], stream=stream.cuda_stream)
+              smem_bytes=tuned["smem_bytes"], warp_cells=tuned.get("warp_cells", -1), stream=stream.cuda_stream)
     slots = [b.add(d["quadrature"], d["n_eq"], d["nx"], d["ny"], d["kn"], d["u0"], d["max_steps"], 1e-3)
              for d in inst]
     torch.cuda.synchronize()
@@ -585,11 +585,15 @@ def run_batch(args):
     b.sync()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    prof = b.run_profile()
     levels = [b.state(sl)["level"] for sl in slots]
     cells = np.array([d["nx"] * d["ny"] for d in inst], dtype=np.float64)
     q = np.array([qmap[d["quadrature"]] for d in inst], dtype=np.float64)
     updates = float(np.sum(cells * np.array(levels)))
     bytes_alg = float(np.sum(cells * np.array(levels) * 2 * q * 4))
+    # the work of the largest 5 % of instances (bytes moved: cells x levels x 2 q x 4)
+    work = cells * np.array(levels) * 2 * q * 4
+    top = np.sort(work)[::-1][: max(1, len(work) // 20)]
     # plain per-instance method on a seeded sample, scaled by cost
     rng = np.random.default_rng(9084523)
     sample = rng.choice(len(inst), size=min(args.plain_sample, len(inst)), replace=False)
@@ -612,7 +616,12 @@ def run_batch(args):
                 "dtype": "f32", "ms_total": round(ms, 3), "instances": len(inst), "finished": int(done),
                 "cell_updates": updates, "algorithmic_bytes": bytes_alg,
                 "achieved_gbs": round(bytes_alg / (ms / 1e3) / 1e9, 1),
-                "launch_shape": {"threads": tuned["threads"], "smem_bytes": tuned["smem_bytes"], "autotuned": True},
+                "launch_shape": {"threads": tuned["threads"], "smem_bytes": tuned["smem_bytes"],
+                                 "warp_cells": tuned.get("warp_cells"), "autotuned": True,
+                                 "searched": tuned.get("searched")},
+                "tail": {"launch_span_s": round(prof["span_s"], 4), "last_cta_alone_s": round(prof["tail_s"], 4),
+                         "tail_share_of_launch": round(prof["tail_s"] / prof["span_s"], 4), "ctas": prof["ctas"],
+                         "largest_5pct_instances_share_of_bytes": round(float(top.sum() / work.sum()), 4)},
                 "gpu_launches": b.launches,
                 "plain_per_instance": {"mlups": round(updates / t_plain_total / 1e6, 2),
                                        "sample": f"{len(sample)} seeded instances alone, same levels, time scaled "

@@ -299,6 +299,10 @@ typedef struct {
     int threads;              /* threads per CTA (64..512, multiple of 32); 0 = 256 */
     int smem_bytes;           /* on-chip instance budget per CTA (bytes); -1 = 96 KiB */
     void *stream;             /* cudaStream_t; NULL = own stream */
+    int warp_cells;           /* instances of at most this many cells are each advanced by one
+                                 warp (a CTA then advances threads/32 of them at once, each with
+                                 its share of the on-chip budget); larger ones by a whole CTA.
+                                 0 = every instance by a CTA; -1 (default) = 512 */
 } lb_batch_params;
 
 typedef struct {
@@ -328,6 +332,12 @@ lb_status lb_batch_history(lb_batch *b, int slot, double *amp, double *shear, in
 lb_status lb_batch_fit(lb_batch *b, int slot, double t_start, double floor_rel, double *rate, int *npoints);
 size_t lb_batch_bytes_in_use(const lb_batch *b);
 long long lb_batch_kernel_launches(const lb_batch *b);
+/* Timing of the last completed batch launch (waits for it): *span_s, the time from the first
+ * CTA's start to the last CTA's end; *tail_s, the time the last CTA ran after every other CTA
+ * had finished (the launch's tail: one instance that no other CTA can share); *ctas, the CTAs
+ * that ran.  Any pointer may be NULL.  LB_ERR_STATE before the first launch.  The paper has
+ * no batching; this measures the persistent multi-instance launch. */
+lb_status lb_batch_run_profile(lb_batch *b, double *span_s, double *tail_s, int *ctas);
 lb_status lb_batch_destroy(lb_batch *b);
 const char *lb_batch_last_error(const lb_batch *b);
 

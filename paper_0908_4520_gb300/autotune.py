@@ -1,7 +1,10 @@
 """Autotuner for the multi-instance launch shape.
 
-The batch kernel's launch shape, threads per CTA and the shared-memory budget
-that decides which instances step on chip, is picked by timed trials: a
+The batch kernel's launch shape is picked by timed trials: threads per CTA, the
+shared-memory budget that decides which instances step on chip, and the tile
+shape of an instance - a whole CTA, or a single warp for instances of at most
+`warp_cells` cells (cells per thread = cells / 32 there, against cells /
+threads on a CTA), so that a CTA advances several small instances at once.  A
 stratified sample of the instance mix is run for a short chunk under each
 candidate shape, and the fastest (cell updates per second) wins.  Results are
 cached in a JSON file keyed by the storage type and a signature of the mix
@@ -17,13 +20,14 @@ import time
 from . import capi
 from .batch import Batch
 
-CANDIDATES = [(t, s) for t in (64, 128, 256) for s in (0, 48 * 1024, 96 * 1024, 200 * 1024)]
+CANDIDATES = [(t, s, w) for t in (64, 128, 256) for s in (0, 48 * 1024, 96 * 1024, 200 * 1024)
+              for w in (0, 256, 1024, 4096)]
 _CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_0908_4520_gb300", "autotune.json")
 
 
 def _signature(instances, precision):
     classes = sorted({(d["quadrature"], d["n_eq"], d["nx"] * d["ny"]) for d in instances})
-    h = hashlib.sha256(json.dumps([precision, classes]).encode()).hexdigest()[:16]
+    h = hashlib.sha256(json.dumps(["threads/smem/warp_cells", precision, classes]).encode()).hexdigest()[:16]
     return f"{precision}:{h}"
 
 
@@ -43,10 +47,10 @@ def _sample(instances, k):
     return out[:k]
 
 
-def _trial(sample, precision, threads, smem, chunk):
+def _trial(sample, precision, threads, smem, warp_cells, chunk):
     import torch
 
-    b = Batch(precision=precision, threads=threads, smem_bytes=smem,
+    b = Batch(precision=precision, threads=threads, smem_bytes=smem, warp_cells=warp_cells,
               budget_bytes=max(1 << 28, 4 * sum(2 * 64 * d["nx"] * d["ny"] * 4 + 8 * (chunk + 2) for d in sample)))
     cells = 0
     for d in sample:
@@ -63,7 +67,7 @@ def _trial(sample, precision, threads, smem, chunk):
 
 
 def tune(instances, precision: str = "f32", sample: int = 48, chunk: int = 64, use_cache: bool = True) -> dict:
-    """Best (threads, smem_bytes) for this mix; cached by mix signature."""
+    """Best (threads, smem_bytes, warp_cells) for this mix; cached by mix signature."""
     sig = _signature(instances, precision)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
@@ -76,16 +80,20 @@ def tune(instances, precision: str = "f32", sample: int = 48, chunk: int = 64, u
         return cache[sig]
     smp = _sample(instances, sample)
     results = []
-    for threads, smem in CANDIDATES:
+    for threads, smem, warp_cells in CANDIDATES:
         try:
-            rate = _trial(smp, precision, threads, smem, chunk)
+            rate = _trial(smp, precision, threads, smem, warp_cells, chunk)
         except capi.LBError:
             continue
-        results.append({"threads": threads, "smem_bytes": smem, "cell_updates_per_s": rate})
+        results.append({"threads": threads, "smem_bytes": smem, "warp_cells": warp_cells,
+                        "cell_updates_per_s": rate})
     if not results:
         raise RuntimeError("no launch shape could run the sample")
     best = max(results, key=lambda r: r["cell_updates_per_s"])
-    entry = {"threads": best["threads"], "smem_bytes": best["smem_bytes"], "trials": results}
+    entry = {"threads": best["threads"], "smem_bytes": best["smem_bytes"], "warp_cells": best["warp_cells"],
+             "trials": results, "searched": {"threads": [64, 128, 256], "smem_bytes": [0, 48 << 10, 96 << 10, 200 << 10],
+                                             "warp_cells (one warp per instance up to; cells per thread = cells/32)":
+                                                 [0, 256, 1024, 4096]}}
     cache[sig] = entry
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)

@@ -7,12 +7,14 @@ from . import capi
 class Batch:
     """Many uneven shear-wave instances advanced by one persistent launch per run.
 
-    precision: "f32", "f16" or "bf16" deviation storage.  threads / smem_bytes:
-    launch shape (0 / -1 = library defaults; the autotuner picks them).
+    precision: "f32", "f16" or "bf16" deviation storage.  threads / smem_bytes / warp_cells:
+    launch shape (0 / -1 / -1 = library defaults; the autotuner picks them): threads per CTA,
+    the CTA's on-chip budget, and the largest instance (cells) advanced by a single warp.
     """
 
     def __init__(self, precision: str = "f32", budget_bytes: int = 1 << 30, max_slots: int = 4096,
-                 threads: int = 0, smem_bytes: int = -1, kn_convention: str = "lambda", stream: int | None = None):
+                 threads: int = 0, smem_bytes: int = -1, kn_convention: str = "lambda", stream: int | None = None,
+                 warp_cells: int = -1):
         p = capi.lb_batch_params_default()
         p.precision = capi.PRECISIONS[precision]
         p.budget_bytes = budget_bytes
@@ -21,6 +23,7 @@ class Batch:
         p.smem_bytes = smem_bytes
         p.kn_convention = capi.KN_LAMBDA if kn_convention == "lambda" else capi.KN_PAPER
         p.stream = stream
+        p.warp_cells = warp_cells
         self.b = capi.lb_batch_create(p)
 
     def add(self, quadrature: str, n_eq: int, nx: int, ny: int, kn: float, u0: float = 1e-3,
@@ -49,6 +52,11 @@ class Batch:
 
     def fit(self, slot: int, t_start: float, floor_rel: float = 1e-4):
         return capi.lb_batch_fit(self.b, slot, t_start, floor_rel)
+
+    def run_profile(self) -> dict:
+        """Span and tail (seconds) of the last completed launch and the CTAs that ran."""
+        span, tail, ctas = capi.lb_batch_run_profile(self.b)
+        return {"span_s": span, "tail_s": tail, "ctas": ctas}
 
     @property
     def bytes_in_use(self) -> int:

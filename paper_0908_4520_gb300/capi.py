@@ -80,7 +80,7 @@ class lb_batch_params(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int), ("kn_convention", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
         ("max_slots", ctypes.c_int), ("threads", ctypes.c_int), ("smem_bytes", ctypes.c_int),
-        ("stream", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p), ("warp_cells", ctypes.c_int),
     ]
 
 
@@ -149,6 +149,7 @@ def _load() -> ctypes.CDLL:
         "lb_batch_bytes_in_use": (ctypes.c_size_t, [H]),
         "lb_batch_kernel_launches": (ctypes.c_longlong, [H]),
         "lb_batch_destroy": (ctypes.c_int, [H]),
+        "lb_batch_run_profile": (ctypes.c_int, [H, dp, dp, ctypes.POINTER(ctypes.c_int)]),
         "lb_batch_last_error": (ctypes.c_char_p, [H]),
         "lb_server_params_default": (None, [ctypes.POINTER(lb_server_params)]),
         "lb_server_create": (ctypes.c_int, [ctypes.POINTER(lb_server_params), ctypes.POINTER(H)]),
@@ -193,6 +194,7 @@ EXPORTS = [
     "lb_server_params_default", "lb_server_create", "lb_server_submit", "lb_server_step", "lb_server_poll",
     "lb_server_history", "lb_server_destroy", "lb_server_last_error", "lb_solve_static", "lb_dvm_run",
     "lb_dvm_run_forced", "lb_diagnostics_at", "lb_halo_bytes", "lb_halo_pack", "lb_halo_unpack",
+    "lb_batch_run_profile",
 ]
 
 
@@ -430,6 +432,13 @@ def lb_batch_fit(b, slot: int, t_start: float, floor_rel: float = 1e-4):
     n = ctypes.c_int()
     check_batch(lib.lb_batch_fit(b, slot, t_start, floor_rel, ctypes.byref(rate), ctypes.byref(n)), b)
     return rate.value, n.value
+
+
+def lb_batch_run_profile(b):
+    """(span_s, tail_s, ctas) of the last completed launch."""
+    span, tail, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    check_batch(lib.lb_batch_run_profile(b, ctypes.byref(span), ctypes.byref(tail), ctypes.byref(n)), b)
+    return span.value, tail.value, n.value
 
 
 def lb_batch_bytes_in_use(b) -> int:

@@ -100,7 +100,10 @@ struct lb_batch {
     lbk::BatchArgs args{};
     lbk::BatchInst* inst_d = nullptr;
     int* order_d = nullptr;
-    int* counters_d = nullptr;  // [0] next, [1] n_order
+    int* counters_d = nullptr;  // [0] next, [1] next_small, [2] n_order, [3] n_small
+    int* order_small_d = nullptr;
+    int warp_cells = 0;
+    unsigned long long* clock_d = nullptr;  // per CTA: start, end of the last launch (%globaltimer, ns)
     std::vector<lbk::BatchInst> inst;
     std::vector<char> live, dirty;
     std::vector<std::vector<std::pair<size_t, size_t>>> ranges_of;
@@ -171,6 +174,7 @@ void lb_batch_params_default(lb_batch_params* p) {
     p->max_slots = 4096;
     p->threads = 0;
     p->smem_bytes = -1;
+    p->warp_cells = -1;
 }
 
 const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
@@ -205,6 +209,7 @@ lb_status lb_batch_create(const lb_batch_params* pin, lb_batch** out) {
     b->p = P;
     b->threads = P.threads ? P.threads : 256;
     b->smem = P.smem_bytes < 0 ? 96 * 1024 : P.smem_bytes;
+    b->warp_cells = P.warp_cells < 0 ? 512 : P.warp_cells;
     auto bail = [&](lb_status s, const std::string& m) {
         g_batch_error = m;
         if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -212,6 +217,8 @@ lb_status lb_batch_create(const lb_batch_params* pin, lb_batch** out) {
         if (b->inst_d) cudaFree(b->inst_d);
         if (b->order_d) cudaFree(b->order_d);
         if (b->counters_d) cudaFree(b->counters_d);
+        if (b->order_small_d) cudaFree(b->order_small_d);
+        if (b->clock_d) cudaFree(b->clock_d);
         if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
         delete b;
         return s;
@@ -244,7 +251,9 @@ lb_status lb_batch_create(const lb_batch_params* pin, lb_batch** out) {
     if (cudaMalloc(&b->arena, P.budget_bytes) != cudaSuccess) return bail(LB_ERR_NOMEM, "arena allocation");
     if (cudaMalloc(&b->inst_d, sizeof(lbk::BatchInst) * P.max_slots) != cudaSuccess ||
         cudaMalloc(&b->order_d, sizeof(int) * P.max_slots) != cudaSuccess ||
-        cudaMalloc(&b->counters_d, 256) != cudaSuccess)
+        cudaMalloc(&b->counters_d, 256) != cudaSuccess ||
+        cudaMalloc(&b->order_small_d, sizeof(int) * P.max_slots) != cudaSuccess ||
+        cudaMalloc(&b->clock_d, sizeof(unsigned long long) * 2 * b->grid) != cudaSuccess)
         return bail(LB_ERR_NOMEM, "descriptor allocation");
     b->ranges.reset(P.budget_bytes);
     b->inst.assign(P.max_slots, lbk::BatchInst{});
@@ -255,11 +264,17 @@ lb_status lb_batch_create(const lb_batch_params* pin, lb_batch** out) {
     b->args.inst = b->inst_d;
     b->args.order = b->order_d;
     b->args.next = b->counters_d;
-    b->args.n_order = b->counters_d + 1;
+    b->args.next_small = b->counters_d + 1;
+    b->args.n_order = b->counters_d + 2;
+    b->args.n_small = b->counters_d + 3;
+    b->args.order_small = b->order_small_d;
     b->args.smem_cap = b->smem;
     b->args.arena = b->arena;
     b->args.hist = static_cast<float2*>(b->arena);
     b->args.trig = static_cast<const float*>(b->arena);
+    b->args.cta_clock = b->clock_d;
+    if ((e = cudaMemsetAsync(b->clock_d, 0, sizeof(unsigned long long) * 2 * b->grid, b->stream)) != cudaSuccess)
+        return bail(LB_ERR_CUDA, cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(b->counters_d, 0, 256, b->stream)) != cudaSuccess)
         return bail(LB_ERR_CUDA, cudaGetErrorString(e));
     *out = b;
@@ -274,8 +289,39 @@ lb_status lb_batch_destroy(lb_batch* b) {
     cudaFree(b->inst_d);
     cudaFree(b->order_d);
     cudaFree(b->counters_d);
+    cudaFree(b->order_small_d);
+    cudaFree(b->clock_d);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
+    return LB_OK;
+}
+
+lb_status lb_batch_run_profile(lb_batch* b, double* span_s, double* tail_s, int* ctas) {
+    if (!b) return LB_ERR_ARG;
+    lb_status st = b->settle();
+    if (st != LB_OK) return st;
+    std::vector<unsigned long long> c(2 * (size_t)b->grid);
+    const cudaError_t e =
+        cudaMemcpy(c.data(), b->clock_d, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return b->cuda_fail(e, "clock read");
+    unsigned long long first = ~0ull, last = 0, second = 0;
+    int n = 0;
+    for (int i = 0; i < b->grid; ++i) {
+        if (c[2 * i + 1] == 0) continue;  // no launch yet
+        ++n;
+        first = std::min(first, c[2 * i]);
+        const unsigned long long end = c[2 * i + 1];
+        if (end > last) {
+            second = last;
+            last = end;
+        } else if (end > second) {
+            second = end;
+        }
+    }
+    if (n == 0) return b->fail(LB_ERR_STATE, "no batch launch has run");
+    if (span_s) *span_s = (double)(last - first) * 1e-9;
+    if (tail_s) *tail_s = n > 1 ? (double)(last - second) * 1e-9 : 0.0;
+    if (ctas) *ctas = n;
     return LB_OK;
 }
 
@@ -383,21 +429,29 @@ lb_status lb_batch_run(lb_batch* b, int chunk) {
     lb_status st = b->settle();
     if (st != LB_OK) return st;
     const int ch = chunk == 0 ? (1 << 30) : chunk;
-    // work list: live, unfinished slots by decreasing remaining cost
-    std::vector<int> order;
+    // work lists: live, unfinished slots by decreasing remaining cost; instances of at most
+    // warp_cells cells go to the warp queue
+    std::vector<int> order, small;
     std::vector<double> cost(b->p.max_slots, 0.0);
     for (int s = 0; s < b->p.max_slots; ++s) {
         if (!b->live[s] || b->inst[s].done) continue;
         const lbk::BatchInst& in = b->inst[s];
         const double levels = std::min<double>(in.max_level - in.level + 1, ch);
         cost[s] = levels * (double)in.nx * in.ny * b->sets[in.set].q;
-        order.push_back(s);
+        ((long long)in.nx * in.ny <= b->warp_cells ? small : order).push_back(s);
     }
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    const int n = (int)order.size();
+    auto by_cost = [&](int x, int y) { return cost[x] > cost[y]; };
+    std::stable_sort(order.begin(), order.end(), by_cost);
+    std::stable_sort(small.begin(), small.end(), by_cost);
+    const int counts[2] = {(int)order.size(), (int)small.size()};
+    const int n = counts[0] + counts[1];
     cudaError_t e = cudaSuccess;
-    if (n) e = cudaMemcpyAsync(b->order_d, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->counters_d + 1, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (counts[0])
+        e = cudaMemcpyAsync(b->order_d, order.data(), sizeof(int) * counts[0], cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && counts[1])
+        e = cudaMemcpyAsync(b->order_small_d, small.data(), sizeof(int) * counts[1], cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->counters_d + 2, counts, sizeof(counts), cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return b->cuda_fail(e, "work list upload");
     if (n == 0) return LB_OK;
     if (!b->graph || b->graph_chunk != ch) {
@@ -407,7 +461,7 @@ lb_status lb_batch_run(lb_batch* b, int chunk) {
         cudaGraph_t g = nullptr;
         if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return b->cuda_fail(e, "cudaStreamBeginCapture");
-        cudaError_t e1 = cudaMemsetAsync(b->counters_d, 0, sizeof(int), b->stream);
+        cudaError_t e1 = cudaMemsetAsync(b->counters_d, 0, 2 * sizeof(int), b->stream);  // both queue heads
         cudaError_t e2 = batch_launch(b);
         e = cudaStreamEndCapture(b->stream, &g);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {

@@ -30,9 +30,11 @@ __device__ __forceinline__ float batch_load(const S* p, float sc) {
     }
 }
 
-// Advance instance `id` by up to B.chunk levels with the CTA's threads.
-template <class VS, int N, class S>
-__device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
+// Advance instance `id` by up to B.chunk levels with the CTA's threads (WARP = false) or with
+// one warp of it (WARP = true: small instances, so that a CTA advances several at once; smem is
+// then the warp's slice of the shared memory, smem_cap bytes).
+template <class VS, int N, class S, bool WARP = false>
+__device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int smem_cap) {
     constexpr int Q = VS::Q;
     BatchInst& in = B.inst[id];
     const Tab<float>& t = B.tab[in.set];
@@ -52,16 +54,25 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
     const float* sinx = B.trig + in.trig_off;
     const float* cosx = sinx + nx;
     float2* hist = B.hist + in.hist_off;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = WARP ? lane : (int)threadIdx.x, nthr = WARP ? 32 : (int)blockDim.x;
+    const int nwarp = (nthr + 31) >> 5;
     __shared__ float red[32][3];
-    __shared__ int s_done;
+    __shared__ int s_done_g[32];
+    int& s_done = s_done_g[WARP ? warp : 0];  // the group's stop flag
+    auto group_sync = [&]() {
+        if constexpr (WARP) {
+            __syncwarp();
+        } else {
+            __syncthreads();
+        }
+    };
 
     int level = in.level;
     int cur = in.cur;
     const int stop = min(in.max_level, level + B.chunk - 1);
     // per-velocity storage scales
-    const bool onchip = 2 * pop * (long long)sizeof(S) <= (long long)B.smem_cap;
+    const bool onchip = 2 * pop * (long long)sizeof(S) <= (long long)smem_cap;
     S* const arena = static_cast<S*>(B.arena);
     S* gbuf[2] = {arena + in.off[0], arena + in.off[1]};
     S* buf[2] = {gbuf[0], gbuf[1]};
@@ -72,7 +83,7 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
             for (long long k = tid; k < pop; k += nthr) buf[cur][k] = gbuf[cur][k];
     }
     if (tid == 0) s_done = in.done;
-    __syncthreads();
+    group_sync();
 
     // 16-bit storage: deviation = stored * sc[a] * scale; sc (tables built with S = 1) and
     // scale are powers of two, so the load and store scales are exact inverses
@@ -149,18 +160,24 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
         ps = warp_sum(ps);
         ph = warp_sum(ph);
         bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) {
+        if (!WARP && lane == 0) {
             red[warp][0] = pa;
             red[warp][1] = ps;
             red[warp][2] = bad ? __int_as_float(0x7fc00000) : ph;
         }
-        __syncthreads();
+        group_sync();
         if (tid == 0) {
             double A = 0, Sx = 0, H = 0;
-            for (int w = 0; w < nwarp; ++w) {
-                A += red[w][0];
-                Sx += red[w][1];
-                H += red[w][2];
+            if constexpr (WARP) {
+                A = pa;
+                Sx = ps;
+                H = bad ? (double)__int_as_float(0x7fc00000) : (double)ph;
+            } else {
+                for (int w = 0; w < nwarp; ++w) {
+                    A += red[w][0];
+                    Sx += red[w][1];
+                    H += red[w][2];
+                }
             }
             const double norm = 2.0 / (double)ncell;
             hist[level] = make_float2((float)(A * norm), (float)(Sx * norm));
@@ -175,7 +192,7 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
             s_done = d;
         }
         cur = (level == 0) ? 0 : 1 - cur;
-        __syncthreads();
+        group_sync();
     }
     if (onchip && level > in.level)
         for (long long k = tid; k < pop; k += nthr) gbuf[cur][k] = buf[cur][k];
@@ -184,14 +201,42 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem) {
         in.cur = cur;
         in.done = s_done;
     }
-    __syncthreads();
+    group_sync();
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <class S, bool WARP>
+__device__ __forceinline__ void batch_dispatch(const BatchArgs& B, int id, S* smem, int smem_cap) {
+    const BatchInst& in = B.inst[id];
+    switch (in.set * 3 + (in.n_eq - 2)) {
+        case 0: batch_run<lbvs::GH4, 2, S, WARP>(B, id, smem, smem_cap); break;
+        case 1: batch_run<lbvs::GH4, 3, S, WARP>(B, id, smem, smem_cap); break;
+        case 2: batch_run<lbvs::GH4, 4, S, WARP>(B, id, smem, smem_cap); break;
+        case 3: batch_run<lbvs::GH6, 2, S, WARP>(B, id, smem, smem_cap); break;
+        case 4: batch_run<lbvs::GH6, 3, S, WARP>(B, id, smem, smem_cap); break;
+        case 5: batch_run<lbvs::GH6, 4, S, WARP>(B, id, smem, smem_cap); break;
+        case 6: batch_run<lbvs::GH8, 2, S, WARP>(B, id, smem, smem_cap); break;
+        case 7: batch_run<lbvs::GH8, 3, S, WARP>(B, id, smem, smem_cap); break;
+        case 8: batch_run<lbvs::GH8, 4, S, WARP>(B, id, smem, smem_cap); break;
+        default: break;
+    }
+}
+
+// Instances come from two work queues ordered longest-first: the CTA queue (each instance
+// advanced by the whole CTA) and, once it is empty, the warp queue (instances of at most
+// warp_cells cells, each advanced by one warp with its slice of the shared memory).
 template <class S>
 __global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char bsm[];
     S* smem = reinterpret_cast<S*>(bsm);
     __shared__ int s_i;
+    // start and end of every CTA (the launch's tail: how long the last CTA runs alone)
+    if (B.cta_clock && threadIdx.x == 0) B.cta_clock[2 * blockIdx.x] = global_ns();
     for (;;) {
         if (threadIdx.x == 0) s_i = atomicAdd(B.next, 1);
         __syncthreads();
@@ -199,21 +244,26 @@ __global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ B
         __syncthreads();
         if (i >= *B.n_order) break;
         const int id = B.order[i];
-        const BatchInst& in = B.inst[id];
-        if (in.done) continue;
-        switch (in.set * 3 + (in.n_eq - 2)) {
-            case 0: batch_run<lbvs::GH4, 2, S>(B, id, smem); break;
-            case 1: batch_run<lbvs::GH4, 3, S>(B, id, smem); break;
-            case 2: batch_run<lbvs::GH4, 4, S>(B, id, smem); break;
-            case 3: batch_run<lbvs::GH6, 2, S>(B, id, smem); break;
-            case 4: batch_run<lbvs::GH6, 3, S>(B, id, smem); break;
-            case 5: batch_run<lbvs::GH6, 4, S>(B, id, smem); break;
-            case 6: batch_run<lbvs::GH8, 2, S>(B, id, smem); break;
-            case 7: batch_run<lbvs::GH8, 3, S>(B, id, smem); break;
-            case 8: batch_run<lbvs::GH8, 4, S>(B, id, smem); break;
-            default: break;
+        if (B.inst[id].done) continue;
+        batch_dispatch<S, false>(B, id, smem, B.smem_cap);
+    }
+    if (B.n_small) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        // each warp's slice of the shared memory, 16-byte aligned
+        const int slice = (B.smem_cap / nwarp) & ~15;
+        S* wsm = reinterpret_cast<S*>(bsm + (size_t)warp * slice);
+        for (;;) {
+            int i = 0;
+            if (lane == 0) i = atomicAdd(B.next_small, 1);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= *B.n_small) break;
+            const int id = B.order_small[i];
+            if (B.inst[id].done) continue;
+            batch_dispatch<S, true>(B, id, wsm, slice);
         }
     }
+    __syncthreads();
+    if (B.cta_clock && threadIdx.x == 0) B.cta_clock[2 * blockIdx.x + 1] = global_ns();
 }
 
 }  // namespace lbk

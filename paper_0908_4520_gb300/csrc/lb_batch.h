@@ -42,6 +42,11 @@ struct BatchArgs {
     float2* hist;
     const float* trig;
     Tab<float> tab[3];    // per set (weights, nodes, Hermite and Lax-Wendroff tables)
+    unsigned long long* cta_clock;  // per CTA: %globaltimer at start and at end (2 grid entries; may be null)
+    // warp queue (may be null): instances of at most warp_cells cells, one warp each
+    const int* order_small;
+    const int* n_small;
+    int* next_small;
 };
 
 cudaError_t batch_launch_f32(const void* args, int grid, int threads, int smem, cudaStream_t st);

@@ -19,9 +19,13 @@ cudaError_t setup_s(int threads, int smem, int* occupancy) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem > optin) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(lb_batch_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         optin - 4096);
+    // (the dynamic limit leaves room for the kernel's own static shared memory)
+    cudaFuncAttributes attr{};
+    cudaError_t e = cudaFuncGetAttributes(&attr, lb_batch_kernel<S>);
+    if (e != cudaSuccess) return e;
+    const int room = optin - (int)attr.sharedSizeBytes;
+    if (smem > room) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(lb_batch_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, lb_batch_kernel<S>, threads, smem);
 }
