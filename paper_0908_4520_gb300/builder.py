@@ -5,6 +5,19 @@ generated translation units so that nvcc can compile them in parallel; the
 host sources (C-ABI, quadrature builder) are compiled alongside, and the
 objects are linked into ``paper_0908_4520_gb300/liblb.so`` against the shared
 CUDA runtime.  Rebuilds only what changed.
+
+Supported build options (environment variables):
+
+* ``LB_EXTRA_NVCC``: extra nvcc flags for every unit, e.g. the launch-shape
+  overrides of ``csrc/lb_kernels.cuh`` (``-DLB_TMA_K=9``, ``-DLB_TMA_BAND=0``,
+  ``-DLB_TMA_WIDE_SMEM=...``; each macro there states its default and what was
+  measured for it);
+* ``LB_BUILD_TAG``: build into ``_build_<tag>/`` and ``liblb_<tag>.so`` instead,
+  so that a library built with other options sits beside the default one
+  (the binding loads it when ``LB_LIB_PATH`` names it);
+* ``LB_UNITS``: a comma list of the generated units to compile (``gh6_f32``,
+  ``d2q37_f32``, ...), for a quick build of one set and storage; a library
+  built this way rejects the other sets with ``LB_ERR_UNSUPPORTED``.
 """
 from __future__ import annotations
 
@@ -27,7 +40,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "177",
               "-I", INCLUDE, "-I", CSRC] + os.environ.get("LB_EXTRA_NVCC", "").split()
-# tuning builds go to their own folder and library name
+# a tagged build goes to its own folder and library name
 if os.environ.get("LB_BUILD_TAG"):
     BUILD = os.path.join(PKG, "_build_" + os.environ["LB_BUILD_TAG"])
     GEN = os.path.join(BUILD, "gen")
@@ -43,7 +56,7 @@ _STORES = {"f32": ("float", "float", "LB_F32"), "f64": ("double", "double", "LB_
 
 
 def _units():
-    """All (set, storage) units, or the subset named in LB_UNITS (comma list) for tuning builds."""
+    """All (set, storage) units, or the subset named in LB_UNITS (comma list)."""
     units = []
     for name, cls, q in _SETS16:
         for st in ("f32", "f64", "bf16", "f16"):
