@@ -296,7 +296,7 @@ typedef struct {
     lb_kn_convention kn_convention;
     size_t budget_bytes;      /* device arena for populations, histories, tables (default 1 GiB) */
     int max_slots;            /* default 4096 */
-    int threads;              /* threads per CTA (64..512, multiple of 32); 0 = 256 */
+    int threads;              /* threads per CTA (64..256, multiple of 32); 0 = 256 */
     int smem_bytes;           /* on-chip instance budget per CTA (bytes); -1 = 96 KiB */
     void *stream;             /* cudaStream_t; NULL = own stream */
     int warp_cells;           /* instances of at most this many cells are each advanced by one

@@ -6,7 +6,10 @@ shape of an instance - a whole CTA, or a single warp for instances of at most
 `warp_cells` cells (cells per thread = cells / 32 there, against cells /
 threads on a CTA), so that a CTA advances several small instances at once.  A
 stratified sample of the instance mix is run for a short chunk under each
-candidate shape, and the fastest (cell updates per second) wins.  Results are
+candidate shape, and the fastest (cell updates per second) wins.  The sample
+holds the whole mix up to 1024 instances: a trial must fill every SM the way the
+real launch does, or it times one instance's latency instead of the launch's
+throughput.  Results are
 cached in a JSON file keyed by the storage type and a signature of the mix
 (quadrature, order and grid-size classes), so later runs reuse them.
 """
@@ -66,7 +69,7 @@ def _trial(sample, precision, threads, smem, warp_cells, chunk):
     return cells * chunk / el
 
 
-def tune(instances, precision: str = "f32", sample: int = 48, chunk: int = 64, use_cache: bool = True) -> dict:
+def tune(instances, precision: str = "f32", sample: int = 1024, chunk: int = 32, use_cache: bool = True) -> dict:
     """Best (threads, smem_bytes, warp_cells) for this mix; cached by mix signature."""
     sig = _signature(instances, precision)
     cache = {}

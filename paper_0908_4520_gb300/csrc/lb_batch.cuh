@@ -6,17 +6,32 @@
 // barrier between levels: an instance never spans CTAs, so no CTA ever waits
 // on another.  An instance whose two population buffers fit the CTA's shared
 // memory is copied in once per chunk and stepped entirely on chip; larger ones
-// step through global memory (L2-resident at these sizes).  The per-cell
-// arithmetic is collide_cell(), the same function the single-lattice kernels
-// call, so a lattice's populations are bitwise the same whichever path runs it
-// and whatever else shares the launch.  Lax-Wendroff streaming only: the
-// batch serves the Gauss-Hermite product sets.
+// step through global memory (L2-resident at these sizes).  A warp advances
+// strips of up to 30 cells of one row: each lane streams one column in y (three
+// loads per velocity) and takes its neighbours' columns by shuffles for the x
+// pass, the two edge lanes streaming the columns beside the strip, as the
+// single-lattice kernels do.  The per-cell arithmetic is collide_cell_pairs(),
+// the collision those kernels call, and a cell's operations do not depend on
+// the path (on chip or through global memory, a CTA or a warp), so an
+// instance's populations are bitwise the same whichever path runs it and
+// whatever else shares the launch.  Lax-Wendroff streaming only: the batch
+// serves the Gauss-Hermite product sets.
 #pragma once
 
 #include "lb_batch.h"
 #include "lb_kernels.cuh"
 
 namespace lbk {
+
+constexpr int kBatchMaxWarps = 8;  // warps per CTA (the kernel's launch bound: 256 threads)
+constexpr int kStrip = 30;  // cells of a row per warp and pass (two lanes stream the columns beside them)
+
+// the kernel's static shared memory (one copy, whichever instance template runs)
+struct BatchShared {
+    float red[kBatchMaxWarps][3];           // per-warp partial sums of a level's diagnostics
+    int done[kBatchMaxWarps];               // stop flag of each group (the CTA, or each warp)
+    float relax[kBatchMaxWarps][4][kMaxNA]; // relaxation tables of each group's instance
+};
 
 template <class S>
 __device__ __forceinline__ float batch_load(const S* p, float sc) {
@@ -34,7 +49,7 @@ __device__ __forceinline__ float batch_load(const S* p, float sc) {
 // one warp of it (WARP = true: small instances, so that a CTA advances several at once; smem is
 // then the warp's slice of the shared memory, smem_cap bytes).
 template <class VS, int N, class S, bool WARP = false>
-__device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int smem_cap) {
+__device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int smem_cap, BatchShared& sh) {
     constexpr int Q = VS::Q;
     BatchInst& in = B.inst[id];
     const Tab<float>& t = B.tab[in.set];
@@ -42,24 +57,24 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
     const int ncell = nx * ny;
     const long long pop = (long long)Q * ncell;
     const float omega = in.omega, sigma_fac = in.sigma_fac;
-    // the instance's relaxation tables (omega W_i and the second terms), in registers
-    float ow_i[VS::NA], owlo_i[VS::NA], hn1lo_i[VS::NA], whn1lo_i[VS::NA];
-#pragma unroll
-    for (int i = 0; i < VS::NA; ++i) {
-        ow_i[i] = in.ow[i];
-        owlo_i[i] = in.owlo[i];
-        hn1lo_i[i] = in.hn1lo[i];
-        whn1lo_i[i] = in.whn1lo[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = WARP ? lane : (int)threadIdx.x, nthr = WARP ? 32 : (int)blockDim.x;
+    const int nwarp = (nthr + 31) >> 5;
+    // the instance's relaxation tables (omega W_i and the second terms of the exact FP32
+    // identities) in shared memory, one copy per group (the CTA, or each warp)
+    float(*rt)[kMaxNA] = sh.relax[WARP ? warp : 0];
+    if (tid < VS::NA) {
+        rt[0][tid] = in.ow[tid];
+        rt[1][tid] = in.owlo[tid];
+        rt[2][tid] = in.hn1lo[tid];
+        rt[3][tid] = in.whn1lo[tid];
     }
     const float* sinx = B.trig + in.trig_off;
     const float* cosx = sinx + nx;
     float2* hist = B.hist + in.hist_off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tid = WARP ? lane : (int)threadIdx.x, nthr = WARP ? 32 : (int)blockDim.x;
-    const int nwarp = (nthr + 31) >> 5;
-    __shared__ float red[32][3];
-    __shared__ int s_done_g[32];
-    int& s_done = s_done_g[WARP ? warp : 0];  // the group's stop flag
+    const int spr = (nx + kStrip - 1) / kStrip;  // strips per row
+    const int nstrip = spr * ny;
+    int& s_done = sh.done[WARP ? warp : 0];  // the group's stop flag
     auto group_sync = [&]() {
         if constexpr (WARP) {
             __syncwarp();
@@ -94,8 +109,17 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
         S* dst = buf[level == 0 ? 0 : 1 - cur];
         float pa = 0.f, ps = 0.f, ph = 0.f;
         bool bad = false;
-        for (int c = tid; c < ncell; c += nthr) {
-            const int y = c / nx, x = c - y * nx;
+        // strips of up to 30 cells of one row, one per warp at a time: lanes 1..w own cells
+        // x0 .. x0 + w - 1; lanes 0 and w + 1 stream the columns beside the strip, so that each
+        // lane streams one column in y and takes its neighbours' columns by shuffles for the x
+        // pass; lanes past w + 1 repeat lane w + 1's column and own nothing
+        for (int s = WARP ? 0 : warp; s < nstrip; s += WARP ? 1 : nwarp) {
+            const int y = s / spr, x0 = (s - y * spr) * kStrip;
+            const int w = min(kStrip, nx - x0);
+            int x = x0 + min(lane, w + 1) - 1;
+            x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            const bool own = lane >= 1 && lane <= w;
+            const int c = y * nx + x;
             float ft[Q];
             if (level == 0) {
                 // f~(0) = f^eq(rho = 1, u_y = u0 sin x, T = 1), rounded through the storage type
@@ -112,21 +136,21 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
                     }
                 });
             } else {
-                const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
                 const int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+                const int om = ym * nx + x, op = yp * nx + x;
+                const bool rows = ny > 1;  // one row: the three y taps read the same value
                 static_for<0, Q>([&](auto ac) {
                     constexpr int a = decltype(ac)::value;
                     constexpr int ix = VS::ix(a), iy = VS::iy(a);
                     const float sc = Is16<S>::value ? t.sc[a] * scale : 1.f;
                     const S* pl = src + (long long)a * ncell;
-                    const float ly0 = t.lw[iy][0], ly1 = t.lw[iy][1], ly2 = t.lw[iy][2];
-                    const float lx0 = t.lw[ix][0], lx1 = t.lw[ix][1], lx2 = t.lw[ix][2];
-                    auto col = [&](int xc) {
-                        return fma(ly0, batch_load<S>(pl + ym * nx + xc, sc),
-                                   fma(ly1, batch_load<S>(pl + y * nx + xc, sc), ly2 * batch_load<S>(pl + yp * nx + xc, sc)));
-                    };
-                    const float gl = col(xm), g0 = col(x), gr = col(xp);
-                    ft[a] = fma(lx0, gl, fma(lx1, g0, lx2 * gr));
+                    const float v0 = batch_load<S>(pl + c, sc);
+                    const float vm = rows ? batch_load<S>(pl + om, sc) : v0;
+                    const float vp = rows ? batch_load<S>(pl + op, sc) : v0;
+                    const float g = fma(t.lw[iy][0], vm, fma(t.lw[iy][1], v0, t.lw[iy][2] * vp));
+                    const float gl = __shfl_up_sync(0xffffffffu, g, 1);
+                    const float gr = __shfl_down_sync(0xffffffffu, g, 1);
+                    ft[a] = fma(t.lw[ix][0], gl, fma(t.lw[ix][1], g, t.lw[ix][2] * gr));
                 });
             }
             // velocity pairs of equal x node as packed f32x2 values (the one-cell-per-lane
@@ -137,33 +161,35 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
                 fp[m] = f2{ft[2 * m], ft[2 * m + 1]};
             });
             const CellOut<float> co = collide_cell_pairs<VS, N, true>(
-                t, ow_i, owlo_i, hn1lo_i, whn1lo_i, 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
+                t, rt[0], rt[1], rt[2], rt[3], 1.f, omega, sigma_fac, in.isothermal, true, false, 0.f, 0.f, 0.f,
                 [&](auto mc) -> f2& { return fp[decltype(mc)::value]; });
-            static_for<0, Q / 2>([&](auto mc) {
-                constexpr int m = decltype(mc)::value;
-                ft[2 * m] = fp[m].x;
-                ft[2 * m + 1] = fp[m].y;
-            });
-            uint32_t r = Is16<S>::value ? sr_seed(level, c) : 0u;
+            if (own) {
+                static_for<0, Q / 2>([&](auto mc) {
+                    constexpr int m = decltype(mc)::value;
+                    ft[2 * m] = fp[m].x;
+                    ft[2 * m + 1] = fp[m].y;
+                });
+                uint32_t r = Is16<S>::value ? sr_seed(level, c) : 0u;
 #pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                if constexpr (Is16<S>::value) r = sr_next(r);
-                dst[(long long)a * ncell + c] =
-                    to_storage<S, float>(ft[a], Is16<S>::value ? t.scinv[a] * inv_scale : 1.f, r);
+                for (int a = 0; a < Q; ++a) {
+                    if constexpr (Is16<S>::value) r = sr_next(r);
+                    dst[(long long)a * ncell + c] =
+                        to_storage<S, float>(ft[a], Is16<S>::value ? t.scinv[a] * inv_scale : 1.f, r);
+                }
+                pa = fma(co.uy, sinx[x], pa);
+                ps = fma(co.sig, cosx[x], ps);
+                ph += co.h;
+                bad |= !isfinite(co.h);
             }
-            pa = fma(co.uy, sinx[x], pa);
-            ps = fma(co.sig, cosx[x], ps);
-            ph += co.h;
-            bad |= !isfinite(co.h);
         }
         pa = warp_sum(pa);
         ps = warp_sum(ps);
         ph = warp_sum(ph);
         bad = __any_sync(0xffffffffu, bad);
         if (!WARP && lane == 0) {
-            red[warp][0] = pa;
-            red[warp][1] = ps;
-            red[warp][2] = bad ? __int_as_float(0x7fc00000) : ph;
+            sh.red[warp][0] = pa;
+            sh.red[warp][1] = ps;
+            sh.red[warp][2] = bad ? __int_as_float(0x7fc00000) : ph;
         }
         group_sync();
         if (tid == 0) {
@@ -174,9 +200,9 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
                 H = bad ? (double)__int_as_float(0x7fc00000) : (double)ph;
             } else {
                 for (int w = 0; w < nwarp; ++w) {
-                    A += red[w][0];
-                    Sx += red[w][1];
-                    H += red[w][2];
+                    A += sh.red[w][0];
+                    Sx += sh.red[w][1];
+                    H += sh.red[w][2];
                 }
             }
             const double norm = 2.0 / (double)ncell;
@@ -211,18 +237,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 template <class S, bool WARP>
-__device__ __forceinline__ void batch_dispatch(const BatchArgs& B, int id, S* smem, int smem_cap) {
+__device__ __forceinline__ void batch_dispatch(const BatchArgs& B, int id, S* smem, int smem_cap, BatchShared& sh) {
     const BatchInst& in = B.inst[id];
     switch (in.set * 3 + (in.n_eq - 2)) {
-        case 0: batch_run<lbvs::GH4, 2, S, WARP>(B, id, smem, smem_cap); break;
-        case 1: batch_run<lbvs::GH4, 3, S, WARP>(B, id, smem, smem_cap); break;
-        case 2: batch_run<lbvs::GH4, 4, S, WARP>(B, id, smem, smem_cap); break;
-        case 3: batch_run<lbvs::GH6, 2, S, WARP>(B, id, smem, smem_cap); break;
-        case 4: batch_run<lbvs::GH6, 3, S, WARP>(B, id, smem, smem_cap); break;
-        case 5: batch_run<lbvs::GH6, 4, S, WARP>(B, id, smem, smem_cap); break;
-        case 6: batch_run<lbvs::GH8, 2, S, WARP>(B, id, smem, smem_cap); break;
-        case 7: batch_run<lbvs::GH8, 3, S, WARP>(B, id, smem, smem_cap); break;
-        case 8: batch_run<lbvs::GH8, 4, S, WARP>(B, id, smem, smem_cap); break;
+        case 0: batch_run<lbvs::GH4, 2, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 1: batch_run<lbvs::GH4, 3, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 2: batch_run<lbvs::GH4, 4, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 3: batch_run<lbvs::GH6, 2, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 4: batch_run<lbvs::GH6, 3, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 5: batch_run<lbvs::GH6, 4, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 6: batch_run<lbvs::GH8, 2, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 7: batch_run<lbvs::GH8, 3, S, WARP>(B, id, smem, smem_cap, sh); break;
+        case 8: batch_run<lbvs::GH8, 4, S, WARP>(B, id, smem, smem_cap, sh); break;
         default: break;
     }
 }
@@ -231,10 +257,11 @@ __device__ __forceinline__ void batch_dispatch(const BatchArgs& B, int id, S* sm
 // advanced by the whole CTA) and, once it is empty, the warp queue (instances of at most
 // warp_cells cells, each advanced by one warp with its slice of the shared memory).
 template <class S>
-__global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(kBatchMaxWarps * 32) lb_batch_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char bsm[];
     S* smem = reinterpret_cast<S*>(bsm);
     __shared__ int s_i;
+    __shared__ BatchShared sh;
     // start and end of every CTA (the launch's tail: how long the last CTA runs alone)
     if (B.cta_clock && threadIdx.x == 0) B.cta_clock[2 * blockIdx.x] = global_ns();
     for (;;) {
@@ -245,7 +272,7 @@ __global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ B
         if (i >= *B.n_order) break;
         const int id = B.order[i];
         if (B.inst[id].done) continue;
-        batch_dispatch<S, false>(B, id, smem, B.smem_cap);
+        batch_dispatch<S, false>(B, id, smem, B.smem_cap, sh);
     }
     if (B.n_small) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -259,7 +286,7 @@ __global__ void __launch_bounds__(256) lb_batch_kernel(const __grid_constant__ B
             if (i >= *B.n_small) break;
             const int id = B.order_small[i];
             if (B.inst[id].done) continue;
-            batch_dispatch<S, true>(B, id, wsm, slice);
+            batch_dispatch<S, true>(B, id, wsm, slice, sh);
         }
     }
     __syncthreads();
