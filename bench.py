@@ -475,6 +475,25 @@ def oracle_throughput(quad, n_eq, rows, warm, steps, kn, scheme="second_order", 
     return procs * 4096 * rows * steps / wall / 1e6, wall
 
 
+def _oracle_grid_job(quad, n_eq, nx, ny, kn, u0, u1, steps):
+    """Wall time of one oracle run of the whole nx x ny grid (a record per level)."""
+    import oracle
+
+    oracle.build()
+    P = oracle.Problem(quad, n_eq, nx, ny, kn)
+    f = P.init_shear(u0, u1)
+    t0 = time.monotonic()
+    P.run(f, steps, record=True)
+    return time.monotonic() - t0
+
+
+def oracle_grid_mlups(quad, n_eq, nx, ny, kn, u0, u1, steps):
+    """Single-thread MLUPS of the oracle on a whole grid, in a spawned process."""
+    with _spawn_pool(1) as ex:
+        wall = ex.submit(_oracle_grid_job, quad, n_eq, nx, ny, kn, u0, u1, steps).result()
+    return nx * ny * steps / wall / 1e6, wall
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -490,13 +509,22 @@ def cpu_baseline(args):
                                  args.streaming, procs=1)
     allc, elc = oracle_throughput(args.quad, args.n_eq, args.cpu_rows, 1, args.cpu_steps, args.kn, args.scheme,
                                   args.streaming, procs=cores)
+    # whole grids, one process: the 64 x 1 FP64 correctness case in full (D2Q16-GH, N = 2,
+    # Kn 0.1, 5000 levels) and the benchmark's problem on a 256^2 grid for a bounded run
+    whole = {}
+    v, w = oracle_grid_mlups("D2Q16-GH", 2, 64, 1, 0.1, 1e-3, 0.0, 5000)
+    whole["64x1 D2Q16-GH N=2, 5000 levels (in full)"] = {"mlups": round(v, 5), "s": round(w, 2)}
+    v, w = oracle_grid_mlups(args.quad, args.n_eq, 256, 256, args.kn, 1e-3, 1e-3, args.cpu_grid_steps)
+    whole[f"256x256 {args.quad} N={args.n_eq}, {args.cpu_grid_steps} levels"] = {"mlups": round(v, 5),
+                                                                                  "s": round(w, 2)}
     return {"value": round(allc, 5), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {args.quad} N={args.n_eq}: {cores} processes (one per host core), each on "
                       f"its own periodic 4096x{args.cpu_rows} slab of the workload, {args.cpu_steps} levels "
                       f"with a record per level ({elc:.1f} s)",
             "single_thread": {"value": round(one, 5), "cores": 1,
                               "sample": f"one process, 4096x{args.cpu_rows} slab, {args.cpu_steps} levels "
-                                        f"({el1:.1f} s)"}}
+                                        f"({el1:.1f} s)"},
+            "whole_grids": whole}
 
 
 def _oracle_rows_job(quad, n_eq, nx, kn, u0, steps, scheme="second_order", streaming="lax_wendroff"):
@@ -971,6 +999,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=0, help="levels of the end-to-end leg (0: --steps)")
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--cpu-grid-steps", type=int, default=40, help="levels of the oracle's whole 256^2 run")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "tma_store"],
                     help="step kernel of the timed lattice (auto: the library's choice)")
