@@ -431,9 +431,10 @@ struct Pack<float, 2> {
 #define LB_TMA_WIDE_SMEM (192 * 1024)
 #endif
 #ifndef LB_DIAG_PREFETCH
-// load sin/cos of the diagnostics before the collision: -1 per set (measured at 4096^2 FP32,
-// TMA kernel, same box: D2Q16-GH 35.7 -> 38.5 GLUPS, D2Q37 12.6 -> 12.6, D2Q36-GH
-// 14.8 -> 11.8, so only D2Q16-GH), 0 never, 1 always
+// load sin/cos of the diagnostics before the collision: -1 per set and kernel (measured at
+// 4096^2 FP32, same box: TMA kernel with plain stores D2Q16-GH 35.7 -> 38.5 GLUPS, D2Q37
+// 12.6 -> 12.6, D2Q36-GH 14.8 -> 11.8; store-staged kernel D2Q36-GH 17.44 -> 17.91; so
+// D2Q16-GH and the store-staged kernel), 0 never, 1 always
 #define LB_DIAG_PREFETCH -1
 #endif
 
@@ -1060,7 +1061,8 @@ __device__ __forceinline__ void collide_store(const Args<R>& A, T (&ft)[VS::Q], 
     const bool forced = (KIND != kStep) && A.force_amp != 0.0;
     // sin(x_i), cos(x_i) of the diagnostics, loaded before the collision so that their
     // latency hides behind it (index clamped: lanes that own no cell add nothing)
-    constexpr bool PF = LB_DIAG_PREFETCH > 0 || (LB_DIAG_PREFETCH < 0 && !VS::kOnLattice && VS::Q == 16);
+    constexpr bool PF =
+        LB_DIAG_PREFETCH > 0 || (LB_DIAG_PREFETCH < 0 && ((!VS::kOnLattice && VS::Q == 16) || OSTRIDE > 0));
     R dsin[V], dcos[V];
     if constexpr (STEP && PF) {
         if (diag) {
