@@ -210,3 +210,31 @@ def test_warp_and_cta_tiles_agree():
     assert prof["ctas"] > 0 and 0 <= prof["tail_s"] <= prof["span_s"]
     w.close()
     c.close()
+
+
+def test_full_mix_sampled_instances_match_oracle():
+    """The batching configuration's own launch: all 512 seeded instances in one persistent
+    launch (the autotuner's default shape), 300 levels each; the smallest instance of each
+    Gauss-Hermite set, sampled from the mix, against the oracle (amplitude history within the
+    FP32 bound of 300 levels)."""
+    from paper_0908_4520_gb300 import inputs
+
+    Batch = batch_cls()
+    inst = inputs.batch_instances(512)
+    b = Batch(budget_bytes=1 << 30)
+    slots = [b.add(d["quadrature"], d["n_eq"], d["nx"], d["ny"], d["kn"], d["u0"], max_steps=300, stop_ratio=0.0)
+             for d in inst]
+    b.run(0).sync()
+    picks = []
+    for q in ("D2Q16-GH", "D2Q36-GH", "D2Q64-GH"):
+        cand = [i for i, d in enumerate(inst) if d["quadrature"] == q]
+        picks.append(min(cand, key=lambda i: (inst[i]["nx"] * inst[i]["ny"], i)))
+    for i in picks:
+        d = inst[i]
+        amp, _ = b.history(slots[i])
+        P = oracle.Problem(d["quadrature"], d["n_eq"], d["nx"], d["ny"], d["kn"])
+        f = P.init_shear(d["u0"])
+        ref = P.run(f, 300)
+        assert len(amp) == 301
+        assert np.max(np.abs(amp - ref[:, 4])) < f32_tol(300) * d["u0"], (d, np.max(np.abs(amp - ref[:, 4])))
+    b.close()

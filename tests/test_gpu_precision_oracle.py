@@ -124,6 +124,44 @@ def test_sixteen_bit_storage_against_oracle(quad, N, kn, prec):
     assert field_err < field_bound, (field_err, field_bound)
 
 
+@functools.lru_cache(maxsize=None)
+def oracle_full_size(kn):
+    P = oracle.Problem("D2Q64-GH", 4, 2048, 1, kn)
+    f = P.init_shear(U0)
+    d = P.run(f, STEPS)
+    return P, d
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_full_size_precision_configuration(prec):
+    """The precision configuration itself, in the benchmark's launch configuration (automatic
+    step kernel): D2Q64-GH, N = 4, 2048 x 2048, U0 = 1e-4, 2000 levels, at the third of the
+    seeded Kn draws (0.062, a monotonic decay), against the oracle's 2048 x 1 run (u_y =
+    U0 sin x does not depend on y): the amplitude history within the storage-noise bound of
+    the module docstring for 2048^2 cells, and the decay rate within the stated 1e-3 (the
+    stochastic-rounding streams are seeded, so the run is deterministic; measured 3e-5 for
+    FP16, 2.5e-4 for BF16)."""
+    Lattice, capi = lib()
+    cfg = inputs.precision_config(_KN[2], prec)
+    L = Lattice(cfg["quadrature"], cfg["n_eq"], cfg["nx"], cfg["ny"], cfg["kn"], precision=prec,
+                diag_capacity=STEPS + 8)
+    L.init_shear_wave(cfg["u0"])
+    L.step(STEPS)
+    rec = L.diagnostics()
+    omega = L.info["omega"]
+    L.close()
+    P, d = oracle_full_size(_KN[2])
+    s = sigma(P, prec)
+    bound = 3.0 * math.sqrt(2.0 * STEPS / (2048 * 2048)) * s + STEPS * omega * 2.0 ** -24
+    amp_err = np.max(np.abs(rec["amp"] - d[:, 4])) / U0
+    assert amp_err < bound, (amp_err, bound)
+    t0 = window(P, d[:, 0])
+    assert monotone_window(d, t0)
+    r_gpu = oracle.decay_fit(rec["t"], rec["amp"], t0)
+    r_ora = oracle.decay_fit(d[:, 0], d[:, 4], t0)
+    assert abs(r_gpu / r_ora - 1.0) < 1e-3, (r_gpu, r_ora)
+
+
 def test_library_fit_equals_the_oracle_rule():
     """lb_fit_decay (FP64, on the device records) and the oracle's fit give the same rate."""
     Lattice, capi = lib()
