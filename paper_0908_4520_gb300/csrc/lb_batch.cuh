@@ -86,7 +86,7 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
     int level = in.level;
     int cur = in.cur;
     const int stop = min(in.max_level, level + B.chunk - 1);
-    // per-velocity storage scales
+    // both buffers of an instance that fits the group's shared memory are stepped on chip
     const bool onchip = 2 * pop * (long long)sizeof(S) <= (long long)smem_cap;
     S* const arena = static_cast<S*>(B.arena);
     S* gbuf[2] = {arena + in.off[0], arena + in.off[1]};
