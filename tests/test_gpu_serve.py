@@ -1,4 +1,5 @@
-"""The request loop: every served result equals the same request solved alone."""
+"""The request loop: every served result equals the same request solved alone, admission
+waits for memory, and a served FP16 stream matches the FP64 oracle request by request."""
 import numpy as np
 import pytest
 
