@@ -213,7 +213,8 @@ __device__ __noinline__ void batch_run(const BatchArgs& B, int id, S* smem, int 
                 in.status |= 1;
                 d = 1;
             }
-            if (level > 0 && (double)H <= (double)in.stop_ratio2 * (double)in.h0) d = 1;
+            // stop rule sqrt(H / H0) <= stop_ratio (none for stop_ratio = 0, also where H is 0)
+            if (level > 0 && in.stop_ratio2 > 0.f && (double)H <= (double)in.stop_ratio2 * (double)in.h0) d = 1;
             if (level == in.max_level) d = 1;
             s_done = d;
         }

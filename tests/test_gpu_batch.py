@@ -115,7 +115,11 @@ def test_budget_admission():
     b.close()
 
 
-@pytest.mark.parametrize("quad,N,nx,ny,kn", [("D2Q16-GH", 2, 64, 1, 0.1), ("D2Q64-GH", 4, 48, 4, 0.7)])
+@pytest.mark.parametrize("quad,N,nx,ny,kn", [("D2Q16-GH", 2, 64, 1, 0.1), ("D2Q64-GH", 4, 48, 4, 0.7),
+                                             # rows narrower than a 30-cell strip, and strips
+                                             # with a ragged tail of 3 and of 1 cell
+                                             ("D2Q36-GH", 3, 2, 1, 0.3), ("D2Q16-GH", 3, 33, 4, 0.2),
+                                             ("D2Q64-GH", 4, 61, 1, 0.5)])
 def test_batch_matches_oracle(quad, N, nx, ny, kn):
     Batch = batch_cls()
     b = Batch()
