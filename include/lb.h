@@ -243,7 +243,9 @@ lb_status lb_synchronize(lb_handle *h);
  * so a lattice stepped one level at a time between exchanges advances its band of the
  * whole grid.  Both calls act on the state the next lb_step reads, are enqueued on the
  * handle's stream (asynchronous; order other streams with events), and copy whole padded
- * rows of every velocity plane.  dst / src: device buffers of lb_halo_bytes bytes, owned by
+ * rows of every velocity plane, as stored: with 16-bit storage every band must use the same
+ * lb_params.storage_scale (the automatic scale follows each band's own initial amplitude).
+ * dst / src: device buffers of lb_halo_bytes bytes, owned by
  * the caller.  LB_ERR_STATE before init; LB_ERR_ARG for a side other than 0, 1 or a NULL
  * buffer.  The paper has no slab decomposition; this is the data-parallel split of its
  * grid. */

@@ -7,8 +7,9 @@ last `gy` rows to its lower and upper neighbours and receives theirs into its
 ghost rows (``lb_halo_pack`` / ``lb_halo_unpack``; the rows move as device
 buffers).  The grid sums of the diagnostics (mass, momentum, the Fourier
 amplitudes of u_y and sigma_xy, the H norm) are combined in FP64 across the
-bands.  This module only schedules and marshals: the populations are stepped,
-packed and unpacked by the library's kernels and copies.
+bands.  The rows travel as stored, so with 16-bit storage every band's lattice takes the
+same `storage_scale`.  This module only schedules and marshals: the populations are
+stepped, packed and unpacked by the library's kernels and copies.
 """
 from __future__ import annotations
 
