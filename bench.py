@@ -382,7 +382,8 @@ def run_gpu(args):
     bpc = main["algorithmic_bytes_per_cell"]
     achieved = main["achieved_gbs"]
     traffic = ncu_traffic(args.quad)
-    cpu = cpu_baseline(args) if not args.no_cpu else None
+    # the oracle on the host cores: at N = 1 only (rank 0), a reported baseline
+    cpu = cpu_baseline(args) if not args.no_cpu and world == 1 else None
     line = {
         "metric": METRIC,
         "value": round(main["mlups"], 2),
